@@ -1,0 +1,447 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 node2vec walk sampler.
+
+Metric: node2vec walk steps/s (real transitions, i.e. written entries != -1)
+and the fraction of the HBM roofline, bit-exact to the CPU oracle, for the
+persistent degree-binned sampler beside the plain one-thread-per-walker,
+one-launch-per-step sampler.
+
+A "step" of this benchmark is one pass of the whole hot path over one batch:
+every walk of the workload (r walks from every vertex, length l) for every
+(p, q) setting of the workload, on a resident graph, through the C ABI.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload rmat20]
+    python bench.py --impl reference ...   # the CPU oracle on the host cores
+
+Under torchrun (N > 1) every rank runs the same per-GPU workload on its own
+range of walk ids (weak scaling, no collective on the data path); the timed
+region is bracketed by barriers and the slowest rank's time is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+REPO = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, REPO)
+
+METRIC = "node2vec walk steps/sec + % HBM roofline, bit-exact; persistent vs plain kernel"
+UNIT = "steps/s"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rmat20")
+    ap.add_argument("--variant", default="persistent", choices=["persistent", "binned", "plain"])
+    ap.add_argument("--compare", default="plain,binned", help="variants timed once beside the main one")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle baseline leg")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--flush-mb", type=int, default=512)
+    ap.add_argument("--tune", default="", help="JSON dict of n2v_tune fields")
+    ap.add_argument("--pq", default="", help="override (p,q) list, e.g. '1,1;0.25,4'")
+    ap.add_argument("--r", type=int, default=0, help="override walks per vertex")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+def csrc_digest() -> str:
+    d = os.path.join(REPO, "paper_1805_00280_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def workload_params(args):
+    from paper_1805_00280_gb300 import graphs as G
+
+    wl = G.WORKLOADS[args.workload]
+    pq = list(wl.pq)
+    if args.pq:
+        pq = [tuple(float(x) for x in s.split(",")) for s in args.pq.split(";")]
+    r = args.r or wl.r
+    return wl, pq, r
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def measured_peak_hbm():
+    p = os.path.join(REPO, "MEASURED_PEAKS.json")
+    try:
+        return float(json.load(open(p))["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def ncu_traffic(workload: str, variant: str):
+    """Per-launch DRAM bytes from a committed ncu summary, if the kernels have not changed since."""
+    p = os.path.join(REPO, "profiles", f"traffic_{variant}_{workload}.json")
+    try:
+        d = json.load(open(p))
+    except Exception:
+        return None
+    if d.get("csrc_sha") != csrc_digest():
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+# --------------------------------------------------------------------------
+# CPU baseline: the oracle, as it stands, on a bounded sample of walk ids
+
+def cpu_oracle_sample(g, starts_np, r, l, pq, seed, budget_s, threads, id_space, rng_seed=0, check=None):
+    import numpy as np
+
+    import oracle
+
+    rng = np.random.default_rng(rng_seed)
+    n_ids = 256
+    done_steps, done_time, sample_desc, parity_ok, parity_rows = 0, 0.0, [], True, 0
+    t_start = time.perf_counter()
+    while True:
+        ids = np.sort(rng.choice(id_space, size=min(n_ids, id_space), replace=False))
+        for (p, q) in pq:
+            t0 = time.perf_counter()
+            rows = oracle.walk(g.row_ptr, g.col, g.w, starts_np, l, p, q, seed, ids, threads=threads)
+            dt = time.perf_counter() - t0
+            done_time += dt
+            done_steps += int((rows >= 0).sum())
+            if check is not None:
+                ok = check(p, q, ids, rows)
+                parity_ok &= ok
+                parity_rows += len(ids)
+        sample_desc.append(len(ids))
+        elapsed = time.perf_counter() - t_start
+        if elapsed > budget_s * 0.5 or n_ids >= id_space:
+            break
+        n_ids = min(id_space, int(n_ids * max(2.0, min(8.0, budget_s * 0.5 / max(elapsed, 1e-3)))))
+    return done_steps, done_time, sample_desc, parity_ok, parity_rows
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+
+    from paper_1805_00280_gb300 import graphs as G
+
+    wl, pq, r = workload_params(args)
+    g = G.workload_graph(wl.name)
+    starts = np.arange(g.n, dtype=np.int32)
+    threads = os.cpu_count() or 1
+    per_step_budget = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    # size the per-step sample once
+    steps_done, t_done, desc, _, _ = cpu_oracle_sample(g, starts, r, wl.l, pq, wl.seed, per_step_budget, threads,
+                                                      g.n * r)
+    n_ids = desc[-1]
+    rng = np.random.default_rng(5)
+    import oracle
+
+    times, steps = [], []
+    for s in range(args.warmup + args.steps):
+        ids = np.sort(rng.choice(g.n * r, size=n_ids, replace=False))
+        t0 = time.perf_counter()
+        st = 0
+        for (p, q) in pq:
+            rows = oracle.walk(g.row_ptr, g.col, g.w, starts, wl.l, p, q, wl.seed, ids, threads=threads)
+            st += int((rows >= 0).sum())
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt)
+            steps.append(st)
+    value = sum(steps) / sum(times)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": wl.name, "n": g.n, "nnz": g.nnz, "r": r, "l": wl.l, "pq": pq,
+                   "sample_walks_per_pq_per_step": n_ids},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{n_ids} random walk ids per (p,q) per step of {g.n * r}"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1805_00280_gb300 import graphs as G
+    from paper_1805_00280_gb300 import n2v
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    wl, pq, r = workload_params(args)
+    t0 = time.perf_counter()
+    g = G.workload_graph(wl.name)
+    gen_s = time.perf_counter() - t0
+    tune = n2v.default_tune(**(json.loads(args.tune) if args.tune else {}))
+    if "hub_count" not in (json.loads(args.tune) if args.tune else {}):
+        tune.hub_count = max(64, g.n // 1000)  # top 0.1% of vertices by degree
+    t0 = time.perf_counter()
+    graph = n2v.Graph.from_csr(g, tune=tune, device=dev)
+    load_s = time.perf_counter() - t0
+    info = graph.info()
+    l = wl.l
+    n_start = g.n
+    W = n_start * r                       # walks per rank
+    r_total = r * world                   # rank k runs rounds [k r, (k+1) r)
+    walk_begin = rank * W
+    starts = torch.arange(n_start, dtype=torch.int32, device=dev)
+    outs = [torch.empty((W, l), dtype=torch.int32, device=dev) for _ in pq]
+    variant = n2v.VARIANTS[args.variant]
+    ws_bytes = max(n2v.n2v_walk_ws_bytes(graph.handle, W, l, variant), 256)
+    ws = torch.empty(ws_bytes // 8 + 32, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(max(args.flush_mb, 1) * (1 << 20) // 4, dtype=torch.int32, device=dev)
+
+    def launch(i, v=variant, out=None):
+        p, q = pq[i]
+        n2v.n2v_walk(graph.handle, starts, n_start, r_total, l, p, q, wl.seed, walk_begin, W,
+                     outs[i] if out is None else out, ws, v, stream)
+
+    for _ in range(args.warmup):
+        for i in range(len(pq)):
+            launch(i)
+    torch.cuda.synchronize(dev)
+    st = n2v.n2v_stream_status(graph.handle, stream)
+    if st != n2v.N2V_OK:
+        raise RuntimeError(f"sampler status {n2v.n2v_strerror(st)}")
+
+    # ---- timed region: K steps, each = every (p,q) job of the workload
+    clocks = ClockSampler(local)
+    evs = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in pq]
+           for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    wall0 = time.perf_counter()
+    for s in range(args.steps):
+        flush.fill_(s)  # evict L2 (129 MB) between steps; outside the events
+        for i in range(len(pq)):
+            evs[s][i][0].record(stream)
+            launch(i)
+            evs[s][i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - wall0
+    barrier()
+    clk = clocks.stop()
+    launch_ms = [[a.elapsed_time(b) for (a, b) in row] for row in evs]
+    total_ms = sum(sum(row) for row in launch_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    st = n2v.n2v_stream_status(graph.handle, stream)
+    if st != n2v.N2V_OK:
+        raise RuntimeError(f"sampler status {n2v.n2v_strerror(st)}")
+
+    # ---- work done per step (deterministic rows, so the same every step)
+    trans, abytes = [], []
+    for i in range(len(pq)):
+        tr, by = n2v.traffic(graph, starts, walk_begin, outs[i])
+        trans.append(tr)
+        abytes.append(by)
+    steps_per_step = sum(trans) * world  # all ranks
+    value = steps_per_step * args.steps / (total_ms / 1e3)
+    mean_launch_ms = [statistics.mean(launch_ms[s][i] for s in range(args.steps)) for i in range(len(pq))]
+
+    # ---- roofline of the dominant kernel (the persistent sampler: one launch per (p,q))
+    peak, peak_kind = measured_peak_hbm()
+    achieved = sum(abytes) / (sum(mean_launch_ms) / 1e3) / 1e9
+    dram = ncu_traffic(wl.name, args.variant)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": dram, "peak_kind": peak_kind,
+                "algorithmic_bytes_per_launch": [int(b) for b in abytes],
+                "kernel": {"persistent": "k_persistent", "binned": "k_binned_step", "plain": "k_plain_step"}[args.variant],
+                "bytes_model": "16 + 4 deg(v) (1+weighted) + [k>=1](16 + 4 deg(t)) + 4 per real transition"}
+
+    # ---- the other variants, once each, and their agreement with the main one
+    compare = {}
+    for vname in [v for v in args.compare.split(",") if v and v != args.variant]:
+        vcode = n2v.VARIANTS[vname]
+        tmp = torch.empty((W, l), dtype=torch.int32, device=dev)
+        ms, same = [], True
+        for i in range(len(pq)):
+            launch(i, vcode, tmp)  # warm-up (also fills tmp)
+            torch.cuda.synchronize(dev)
+            flush.fill_(7)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            launch(i, vcode, tmp)
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            ms.append(a.elapsed_time(b))
+            same &= bool(torch.equal(tmp, outs[i]))
+        del tmp
+        compare[vname] = {"value": sum(trans) * world / (sum(ms) / 1e3), "unit": UNIT, "ms_per_step": sum(ms),
+                          "bit_identical_to_" + args.variant: same,
+                          "launches_per_step": len(pq) * (l if vname != "persistent" else 1)}
+    if compare.get("plain"):
+        compare["speedup_over_plain"] = value / compare["plain"]["value"]
+
+    # ---- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        starts_h = torch.arange(n_start, dtype=torch.int32).pin_memory()
+        out_h = torch.empty((W, l), dtype=torch.int32).pin_memory()
+        starts_d = torch.empty_like(starts)
+        K2 = max(1, min(args.steps, 3))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        torch.cuda.synchronize(dev)
+        a.record(stream)
+        for s in range(K2):
+            for i in range(len(pq)):
+                starts_d.copy_(starts_h, non_blocking=True)
+                p, q = pq[i]
+                n2v.n2v_walk(graph.handle, starts_d, n_start, r_total, l, p, q, wl.seed, walk_begin, W, outs[i], ws,
+                             variant, stream)
+                out_h.copy_(outs[i], non_blocking=True)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        e2e_ms = a.elapsed_time(b)
+        if world > 1:
+            t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        e2e = {"value": steps_per_step * K2 / (e2e_ms / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": 4 * n_start * len(pq), "d2h_bytes_per_step": 4 * W * l * len(pq),
+               "steps": K2, "path": "pinned host starts -> n2v_walk -> pinned host walks, per (p,q)"}
+        del out_h
+
+    # ---- CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only)
+    cpu = None
+    parity = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        starts_np = np.arange(n_start, dtype=np.int32)
+        threads = os.cpu_count() or 1
+        out_np_cache = {}
+
+        def check(p, q, ids, rows):
+            i = pq.index((p, q))
+            got = outs[i][torch.from_numpy(ids).to(dev)].cpu().numpy()
+            return bool(np.array_equal(got, rows))
+
+        steps_c, t_c, desc, ok, nrows = cpu_oracle_sample(g, starts_np, r, l, pq, wl.seed, args.cpu_seconds, threads,
+                                                          W, check=check)
+        cpu = {"value": steps_c / t_c, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"random walk-id samples of sizes {desc} per (p,q) out of {W}"}
+        parity = {"oracle_rows_checked": nrows, "bit_exact": ok}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": wl.name, "desc": wl.note, "n": g.n, "nnz": g.nnz, "weighted": g.w is not None,
+                   "r": r, "l": l, "pq": pq, "walks_per_gpu": W, "variant": args.variant,
+                   "tune": tune.as_dict(), "hubs": info.hub_count, "hub_min_degree": info.hub_min_degree,
+                   "max_degree": info.max_degree,
+                   "l2": f"flushed between steps ({args.flush_mb} MB write); output {4 * W * l * len(pq) >> 20} MB",
+                   "gen_s": round(gen_s, 2), "load_s": round(load_s, 3)},
+        "walks_per_s": W * len(pq) * world * args.steps / (total_ms / 1e3),
+        "nominal_steps_per_s": W * l * len(pq) * world * args.steps / (total_ms / 1e3),
+        "real_transitions_per_step": steps_per_step,
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": args.steps * len(pq) * (1 if args.variant == "persistent" else l),
+        "clocks": clk,
+        "compare": compare,
+        "parity": parity,
+        "wall_s_timed": wall,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    graph.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

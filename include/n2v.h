@@ -1,0 +1,193 @@
+/*
+ * n2v.h -- C ABI of the GB300 (sm_103a) node2vec 2nd-order walk sampler.
+ *
+ * The library generates node2vec biased random walks (Zhou, Niu, Chen,
+ * "Efficient Graph Computation for Node2Vec", arXiv 1805.00280) with every
+ * transition distribution computed on the fly at the step that needs it
+ * (Section 3.2), instead of stored per edge (Eq. 1 gives the memory the stored
+ * form would take: 8 * sum_i d_i^2 bytes).
+ *
+ * Walk model (Section 2.1 and Algorithm 1).  A walker at v that arrived from t
+ * gives each out-neighbour x of v the weight w(v,x) * alpha(t,x), with
+ * alpha = 1/p if x == t, 1 if x is an out-neighbour of t, and 1/q otherwise;
+ * the first step (superstep 0 of Algorithm 1) has no t and uses w(v,x)
+ * alone.  A walk stores its l sampled vertices (the start is not stored).
+ *
+ * Integer contract (the same on every variant, so results are bit-exact):
+ *   - alpha in Q16 fixed point, rounded once on the host:
+ *       a_p = round_half_even(65536 / p), a_q = round_half_even(65536 / q),
+ *       the return-free common-neighbour value is 65536;
+ *   - c_x = w(v,x) * alpha as uint64, T = sum over N(v) (w == 1 if unweighted);
+ *   - u = Philox4x32-10 (Salmon et al., SC'11) with key (lo32 seed, hi32 seed)
+ *     and counter (k, lo32 walk_id, hi32 walk_id, 0), u = out[1]<<32 | out[0];
+ *   - r = floor(u * T / 2^64); the chosen x is the first neighbour in CSR
+ *     order whose inclusive prefix sum of c exceeds r;
+ *   - T == 0 (no out-edges or all weights zero) ends the walk: that step and
+ *     the later ones are written as -1.
+ *
+ * Graph: CSR with int64 row_ptr[n+1] (row_ptr[0] == 0, non-decreasing,
+ * row_ptr[n] == nnz), int32 col[nnz] strictly increasing inside every row and
+ * in [0, n), optional uint32 weights w[nnz].  Directed graphs use out-lists
+ * (Section 3.2 analyses the undirected case and notes that directed graphs
+ * work alike).
+ *
+ * Memory: the library never allocates device memory.  Every device buffer
+ * (graph arrays, the auxiliary buffer, walk workspace, output) is owned by the
+ * caller, who must keep it alive while the library uses it.  The library
+ * allocates small host structures (the graph handle) with malloc.
+ *
+ * Streams: `stream` arguments are cudaStream_t values passed as void*
+ * (NULL = the legacy default stream).  n2v_walk is asynchronous; argument
+ * errors are returned synchronously, errors found on the device (a start
+ * vertex out of range) are recorded in a device status word that
+ * n2v_stream_status reads.
+ *
+ * Thread safety: distinct graph handles may be used from distinct threads.
+ * Calls on one handle that overlap in time must use one stream.
+ */
+#ifndef N2V_H
+#define N2V_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes -------------------------------------------------------- */
+#define N2V_OK 0
+#define N2V_ERR_INVALID_ARG (-1)   /* a bad argument (null pointer, size, p, q ...) */
+#define N2V_ERR_INVALID_GRAPH (-2) /* CSR is not canonical (see above)              */
+#define N2V_ERR_OVERFLOW (-3)      /* max_v sum_x w(v,x) * max(a_p, 65536, a_q) >= 2^64 */
+#define N2V_ERR_NO_MEM (-4)        /* a caller buffer is smaller than required       */
+#define N2V_ERR_TIMEOUT (-5)       /* a bounded device wait gave up                  */
+#define N2V_ERR_CUDA (-6)          /* a CUDA runtime call failed                     */
+
+/* ---- sampler variants (n2v_walk `variant`) ------------------------------- */
+/* One thread per walker and one launch per step (the plain form). */
+#define N2V_PLAIN 0
+/* One launch per step; inside it each warp serves 32 walkers and hands every
+ * step whose degrees exceed the thread threshold to the whole warp. */
+#define N2V_BINNED 1
+/* One persistent launch for all steps of all walkers: warps take batches of
+ * walkers from a device work counter and run all l steps, binning each step
+ * by degree (one lane, or the whole warp). */
+#define N2V_PERSISTENT 2
+/* Flag: record the launch sequence of the call as a CUDA graph the first time
+ * a shape is seen on a handle, and replay it afterwards. */
+#define N2V_FLAG_CUDA_GRAPH 0x100
+
+/* ---- tuning ---------------------------------------------------------------- */
+typedef struct n2v_tune {
+  int32_t block_threads;   /* threads per block of the binned/persistent kernels (64..1024, x32) */
+  int32_t blocks_per_sm;   /* resident blocks per SM for the persistent grid; 0 = occupancy max */
+  int32_t thread_max_deg;  /* a step runs on one lane when deg(v) and deg(t) are <= this      */
+  int32_t smem_specials;   /* per-warp shared-memory slots for the special positions of a step */
+  int32_t hub_count;       /* vertices (largest degree first) with a hashed neighbour set     */
+  int32_t hub_min_degree;  /* a vertex needs at least this degree to get a hashed set         */
+  int32_t chunk_walkers;   /* walkers per persistent launch (0 = all in one launch)           */
+  int32_t hub_budget_mb;   /* MiB of device memory for all hub hash sets (8 bytes per slot)   */
+  int32_t reserved[8];     /* must be zero                                                    */
+} n2v_tune;
+
+/* Fill *t with the library defaults. */
+void n2v_tune_default(n2v_tune* t);
+
+/* ---- graph ----------------------------------------------------------------- */
+typedef struct n2v_graph n2v_graph; /* opaque handle */
+
+typedef struct n2v_graph_info {
+  int64_t n, nnz;
+  int32_t weighted;
+  int32_t hub_count;      /* hubs that received a hashed neighbour set */
+  int64_t max_degree;
+  uint64_t max_wsum;      /* max over v of sum_x w(v,x) (= max degree when unweighted) */
+  int64_t hub_min_degree; /* smallest degree among the hubs (0 if none) */
+  int64_t hub_slots;      /* total slots of all hub hash sets */
+  int64_t deg_hist[34];   /* [0]: degree 0; [i>=1]: degree in [2^(i-1), 2^i) */
+} n2v_graph_info;
+
+/* Bytes of device memory the caller must provide as `aux` to n2v_graph_load
+ * for a graph of this size under tuning `t` (NULL = defaults).  Holds the
+ * device status word, degree statistics, the per-edge static weight prefix of
+ * weighted graphs (8 bytes per entry) and the hub neighbour-set cache (the
+ * GPU counterpart of the FN-Cache neighbour cache, Section 3.4). */
+int n2v_graph_aux_bytes(int64_t n, int64_t nnz, int weighted, const n2v_tune* t, size_t* bytes);
+
+/* Validate a device-resident CSR graph and build its auxiliary structures in
+ * `aux` (device memory of at least n2v_graph_aux_bytes bytes, 256-byte
+ * aligned).  row_ptr, col, w and aux are BORROWED device pointers: the
+ * caller keeps them alive until n2v_graph_free.  w may be NULL (unweighted).
+ * Synchronises `stream` (this is set-up, not the hot path).  Returns
+ * N2V_ERR_INVALID_GRAPH for a non-canonical CSR, N2V_ERR_NO_MEM when
+ * aux_bytes is too small.  On success *out receives a new handle. */
+int n2v_graph_load(const int64_t* row_ptr, const int32_t* col, const uint32_t* w, int64_t n, int64_t nnz,
+                   void* aux, size_t aux_bytes, const n2v_tune* t, void* stream, n2v_graph** out);
+
+/* Host copy of the statistics computed at load. */
+int n2v_graph_info_get(const n2v_graph* g, n2v_graph_info* info);
+
+/* Replace the tuning of a loaded graph.  Fields that size `aux` (hub_count,
+ * hub_min_degree) must not grow beyond what aux was sized for; the hub cache
+ * is rebuilt on `stream`.  Synchronises `stream`. */
+int n2v_graph_retune(n2v_graph* g, const n2v_tune* t, void* stream);
+
+/* Release the handle (and any CUDA graphs recorded on it).  Device buffers
+ * stay the caller's. */
+void n2v_graph_free(n2v_graph* g);
+
+/* ---- walks ----------------------------------------------------------------- */
+
+/* Bytes of device workspace n2v_walk needs for `walk_count` walks of length l
+ * with `variant` (0 is a valid answer; ws may then be NULL). */
+int n2v_walk_ws_bytes(const n2v_graph* g, int64_t walk_count, int32_t l, int variant, size_t* bytes);
+
+/* Generate walks with ids [walk_begin, walk_begin + walk_count) of the job
+ * "r walks from each of the n_starts vertices in `starts`" (Section 2.1: r
+ * walks of length l per vertex).  Walk ids are round-major: id = round *
+ * n_starts + i starts at starts[i], so one call, or any split of the id range
+ * into several calls (chunking as in FN-Multi, Section 3.4; sharding over
+ * devices), gives the same rows.
+ *   starts   device int32 [n_starts], each in [0, n)
+ *   walks    device int32 [walk_count][l], row-major; row i is walk id
+ *            walk_begin + i
+ *   ws       device workspace of n2v_walk_ws_bytes bytes (256-byte aligned)
+ *   p, q     node2vec return / in-out parameters, finite and > 0, with
+ *            65536/p and 65536/q rounding into [1, 2^24]
+ *   seed     Philox key
+ *   variant  N2V_PLAIN, N2V_BINNED or N2V_PERSISTENT, optionally | N2V_FLAG_CUDA_GRAPH
+ * Asynchronous on `stream`.  Returns N2V_ERR_OVERFLOW when the weighted
+ * totals could exceed 64 bits for these p, q.  A start vertex out of range
+ * writes -1 rows and sets N2V_ERR_INVALID_ARG in the status word. */
+int n2v_walk(const n2v_graph* g, const int32_t* starts, int64_t n_starts, int32_t r, int32_t l, double p,
+             double q, uint64_t seed, int64_t walk_begin, int64_t walk_count, int32_t* walks, void* ws,
+             size_t ws_bytes, int variant, void* stream);
+
+/* Q16 return parameters exactly as n2v_walk rounds them (host function). */
+int n2v_alpha_q16(double p, double q, uint32_t* a_p, uint32_t* a_q);
+
+/* Count, over walk rows [walk_begin, walk_begin + walk_count) that n2v_walk
+ * wrote to `walks`, the real transitions (entries != -1) and the adjacency
+ * bytes of the per-step model of Section 3.2 (N(v) read locally, N(t) as the
+ * NEIG message): 16 + 4*deg(v)*(1 + weighted) + [k >= 1]*(16 + 4*deg(t)) + 4.
+ * out2 is DEVICE uint64[2] and is overwritten: out2[0] = transitions,
+ * out2[1] = bytes.  Asynchronous on `stream`. */
+int n2v_walk_traffic(const n2v_graph* g, const int32_t* starts, int64_t n_starts, int64_t walk_begin,
+                     int64_t walk_count, int32_t l, const int32_t* walks, uint64_t* out2, void* stream);
+
+/* Synchronise `stream`, return and clear the device status word of `g`
+ * (N2V_OK, N2V_ERR_INVALID_ARG or N2V_ERR_TIMEOUT), or N2V_ERR_CUDA when the
+ * stream reports a CUDA error. */
+int n2v_stream_status(const n2v_graph* g, void* stream);
+
+/* Static text for a status code. */
+const char* n2v_strerror(int code);
+
+/* Number of SMs and the persistent grid the handle would launch. */
+int n2v_launch_shape(const n2v_graph* g, int32_t* sms, int32_t* blocks, int32_t* threads);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* N2V_H */

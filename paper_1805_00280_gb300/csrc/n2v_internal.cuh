@@ -1,0 +1,210 @@
+// Internal declarations and device primitives of the GB300 node2vec sampler.
+//
+// Shared by the graph set-up, the samplers and the serving loop.  Nothing here
+// is visible through the C ABI (include/n2v.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "n2v.h"
+
+namespace n2v {
+
+constexpr uint32_t kAlphaOne = 65536u;  // alpha = 1 in Q16
+constexpr unsigned kFull = 0xffffffffu;
+
+// device status word bits
+constexpr uint32_t kStInvalidArg = 1u;
+constexpr uint32_t kStTimeout = 2u;
+constexpr uint32_t kStInternal = 4u;  // a self-check of the sampler failed
+
+// Read-only view of a resident graph plus its auxiliary structures.
+struct GraphView {
+  const int64_t* __restrict__ rp;      // [n+1]
+  const int32_t* __restrict__ col;     // [nnz]
+  const uint32_t* __restrict__ w;      // [nnz] or null (unweighted)
+  const uint64_t* __restrict__ wpre;   // [nnz] row-local inclusive prefix of w (weighted only)
+  int64_t n;
+  // hashed neighbour sets of hub vertices (FN-Cache analogue); hub_of null = none
+  const int32_t* __restrict__ hub_of;    // [n] hub slot or -1
+  const int64_t* __restrict__ hub_off;   // [H] first slot of the hub's table
+  const uint32_t* __restrict__ hub_bits; // [H] log2 of the table size
+  const int2* __restrict__ hub_slot;     // [slots] (neighbour id or -1 if empty, index in the hub's row)
+};
+
+// One walk job slice, as every sampler sees it.
+struct WalkJob {
+  const int32_t* starts;
+  int64_t n_starts;
+  int64_t walk_begin;  // first walk id of this slice
+  int64_t count;       // walks in this slice
+  int32_t l;
+  uint32_t a_p, a_q;
+  uint64_t seed;
+  int32_t* walks;      // [count][l]
+  uint32_t* status;
+};
+
+// Tuning resolved for a launch.
+struct LaunchCfg {
+  int block_threads;
+  int blocks;
+  int thread_max_deg;
+  int smem_specials;  // per warp
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of the
+// multiply-xor bijection with the key advanced by the Weyl increments between
+// rounds.  Key = (lo32 seed, hi32 seed); counter = (k, lo32 id, hi32 id, 0);
+// the 64-bit draw is out[1] << 32 | out[0].
+__device__ __forceinline__ uint64_t philox_draw(uint64_t seed, uint64_t walk_id, uint32_t k) {
+  uint32_t x0 = k, x1 = (uint32_t)walk_id, x2 = (uint32_t)(walk_id >> 32), x3 = 0u;
+  uint32_t key0 = (uint32_t)seed, key1 = (uint32_t)(seed >> 32);
+#pragma unroll
+  for (int i = 0; i < 10; ++i) {
+    const uint32_t m0 = 0xD2511F53u, m1 = 0xCD9E8D57u;
+    uint32_t hi0 = __umulhi(m0, x0), lo0 = m0 * x0;
+    uint32_t hi1 = __umulhi(m1, x2), lo1 = m1 * x2;
+    uint32_t y0 = hi1 ^ x1 ^ key0;
+    uint32_t y2 = hi0 ^ x3 ^ key1;
+    x0 = y0;
+    x1 = lo1;
+    x2 = y2;
+    x3 = lo0;
+    key0 += 0x9E3779B9u;
+    key1 += 0xBB67AE85u;
+  }
+  return ((uint64_t)x1 << 32) | (uint64_t)x0;
+}
+
+// floor(u * T / 2^64)
+__device__ __forceinline__ uint64_t scale_draw(uint64_t u, uint64_t T) { return __umul64hi(u, T); }
+
+// First index i in [0, n) with a[i] >= key (n if none).
+__device__ __forceinline__ int64_t lower_bound_i32(const int32_t* __restrict__ a, int64_t n, int32_t key) {
+  int64_t lo = 0;
+  while (n > 0) {
+    int64_t half = n >> 1;
+    if (__ldg(a + lo + half) < key) {
+      lo += half + 1;
+      n -= half + 1;
+    } else {
+      n = half;
+    }
+  }
+  return lo;
+}
+
+__device__ __forceinline__ bool contains_i32(const int32_t* __restrict__ a, int64_t n, int32_t key) {
+  int64_t i = lower_bound_i32(a, n, key);
+  return i < n && __ldg(a + i) == key;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+__device__ __forceinline__ uint64_t warp_sum_u64(uint64_t x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+  return x;
+}
+
+__device__ __forceinline__ uint64_t warp_incl_scan_u64(uint64_t x, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint64_t y = __shfl_up_sync(kFull, x, o);
+    if (lane >= o) x += y;
+  }
+  return x;
+}
+
+// First index j in [lo, hi] with a[j] > key, given a non-decreasing a and
+// a[hi] > key.  Whole warp, 32-ary search.
+__device__ __forceinline__ int64_t warp_first_above_u64(const uint64_t* __restrict__ a, int64_t lo,
+                                                        int64_t hi, uint64_t key, int lane) {
+  while (hi - lo + 1 > 32) {
+    int64_t step = (hi - lo + 32) / 32;  // ceil(len / 32)
+    int64_t p = lo + (int64_t)(lane + 1) * step - 1;
+    if (p > hi) p = hi;
+    unsigned m = __ballot_sync(kFull, __ldg(a + p) > key);
+    if (!m) return hi;     // lane 31 probes hi, so this only happens if a[hi] <= key
+    int f = __ffs(m) - 1;
+    int64_t pf = __shfl_sync(kFull, p, f);
+    int64_t pprev = __shfl_sync(kFull, p, f > 0 ? f - 1 : 0);
+    hi = pf;
+    if (f > 0) lo = pprev + 1;
+  }
+  int64_t p = lo + lane;
+  unsigned m = __ballot_sync(kFull, p <= hi && __ldg(a + p) > key);
+  return m ? lo + (__ffs(m) - 1) : hi;
+}
+
+}  // namespace n2v
+
+// Host-side handle.
+struct n2v_graph {
+  n2v::GraphView view;
+  int64_t n, nnz;
+  int weighted;
+  void* aux;
+  size_t aux_bytes;
+  uint32_t* status;        // device status word
+  unsigned long long* scratch;  // device scratch words inside aux
+  n2v_tune tune;
+  n2v_graph_info info;
+  int device;
+  int sms;
+  void* graph_cache;       // recorded CUDA graphs (opaque, see n2v_walk.cu)
+};
+
+namespace n2v {
+
+// Fibonacci hashing of a vertex id into a table of 2^bits slots.
+__host__ __device__ __forceinline__ uint32_t hub_hash(int32_t x, uint32_t bits) {
+  return ((uint32_t)x * 2654435769u) >> (32u - bits);
+}
+
+// Index of x inside the CSR row of hub h, or -1 when x is not a neighbour.
+// Linear probing over a table at most half full; every probe sequence ends at
+// an empty slot or at x, and is additionally bounded by the table size.
+__device__ __forceinline__ int32_t hub_find(const GraphView& g, int32_t h, int32_t x) {
+  const int2* __restrict__ tab = g.hub_slot + g.hub_off[h];
+  const uint32_t bits = g.hub_bits[h];
+  const uint32_t mask = (1u << bits) - 1u;
+  uint32_t s = hub_hash(x, bits);
+  for (uint32_t probe = 0; probe <= mask; ++probe) {
+    int2 e = __ldg(tab + s);
+    if (e.x == x) return e.y;
+    if (e.x < 0) return -1;
+    s = (s + 1u) & mask;
+  }
+  return -1;
+}
+
+// Layout of the caller's auxiliary buffer (byte offsets, 256-aligned).
+struct AuxLayout {
+  size_t status, scratch, wpre, hub_of, hub_off, hub_bits, hub_vtx, hub_slot, total;
+  int64_t hubs_cap, slots_cap;
+};
+AuxLayout aux_layout(int64_t n, int64_t nnz, int weighted, const n2v_tune& t);
+
+// scratch word indices (unsigned long long) inside the aux scratch block
+enum : int {
+  kScBad = 0,
+  kScMaxDeg = 1,
+  kScMaxWsum = 2,
+  kScHubCount = 3,
+  kScSlotCount = 4,
+  kScHist = 8,  // 34 words
+  kScWords = 64
+};
+
+// n2v_walk.cu
+LaunchCfg resolve_launch(const n2v_graph* g, int variant);
+void free_graph_cache(n2v_graph* g);
+}  // namespace n2v

@@ -1,0 +1,413 @@
+// The three samplers (plain, binned, persistent), their launch logic, the
+// CUDA-graph recording of a call's launch sequence, and the walk-traffic
+// counter.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "n2v_step.cuh"
+
+namespace n2v {
+
+// ---------------------------------------------------------------------------
+// Plain: one thread per walker, one launch per step k.  The walker's state is
+// read back from its own output row (v = row[k-1], t = row[k-2] or the start).
+__global__ void __launch_bounds__(256) k_plain_step(GraphView g, WalkJob J, int k) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= J.count) return;
+  const int64_t wid = J.walk_begin + i;
+  int32_t* row = J.walks + i * (int64_t)J.l;
+  const int64_t s0 = J.starts[wid % J.n_starts];
+  if (s0 < 0 || s0 >= g.n) {
+    if (k == 0) atomicOr(J.status, kStInvalidArg);
+    row[k] = -1;
+    return;
+  }
+  int64_t v, t;
+  if (k == 0) {
+    v = s0;
+    t = -1;
+  } else {
+    v = row[k - 1];
+    if (v < 0) {
+      row[k] = -1;
+      return;
+    }
+    t = (k == 1) ? s0 : row[k - 2];
+  }
+  row[k] = thread_step(g, t, v, k, philox_draw(J.seed, (uint64_t)wid, (uint32_t)k), J.a_p, J.a_q);
+}
+
+// ---------------------------------------------------------------------------
+// Binned: one launch per step k; warp w owns walkers [32w, 32w + 32) and bins
+// each of their steps by degree (own lane, or the whole warp).
+__global__ void k_binned_step(GraphView g, WalkJob J, int k, int thr, int cap) {
+  extern __shared__ uint32_t smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t* sbuf = smem + warp * cap;
+  const int64_t base = ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * 32;
+  if (base >= J.count) return;  // uniform per warp
+  const int64_t i = base + lane;
+  const bool mine = i < J.count;
+  const int64_t wid = J.walk_begin + i;
+  int32_t* row = J.walks + i * (int64_t)J.l;
+  bool alive = false;
+  int64_t v = -1, t = -1;
+  if (mine) {
+    const int64_t s0 = J.starts[wid % J.n_starts];
+    if (s0 >= 0 && s0 < g.n) {
+      if (k == 0) {
+        v = s0;
+        alive = true;
+      } else {
+        v = row[k - 1];
+        t = (k == 1) ? s0 : row[k - 2];
+        alive = v >= 0;
+      }
+    } else if (k == 0) {
+      atomicOr(J.status, kStInvalidArg);
+    }
+  }
+  const int32_t x = warp_binned_step(g, alive, t, v, k, (uint64_t)wid, J.seed, J.a_p, J.a_q, thr, sbuf, cap, lane);
+  if (mine) row[k] = alive ? x : -1;
+}
+
+// ---------------------------------------------------------------------------
+// Persistent: one launch for all l steps.  Each warp takes 32 walkers at a
+// time from a device counter and runs them to the end; every step is binned
+// by degree as above.  Walkers are independent (FN-Multi's observation,
+// Section 3.4), so the order in which warps take them does not change any row.
+__global__ void k_persistent(GraphView g, WalkJob J, unsigned long long* __restrict__ counter, int thr, int cap) {
+  extern __shared__ uint32_t smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t* sbuf = smem + warp * cap;
+  for (;;) {
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(counter, 32ull);
+    base = __shfl_sync(kFull, base, 0);
+    if ((int64_t)base >= J.count) break;
+    const int64_t i = (int64_t)base + lane;
+    const bool mine = i < J.count;
+    const int64_t wid = J.walk_begin + i;
+    int32_t* row = J.walks + i * (int64_t)J.l;
+    int64_t t = -1, v = -1;
+    bool alive = false;
+    if (mine) {
+      const int64_t s0 = J.starts[wid % J.n_starts];
+      if (s0 >= 0 && s0 < g.n) {
+        v = s0;
+        alive = true;
+      } else {
+        atomicOr(J.status, kStInvalidArg);
+      }
+    }
+    for (int k = 0; k < J.l; ++k) {
+      if (!__any_sync(kFull, alive)) {
+        if (mine)
+          for (int kk = k; kk < J.l; ++kk) row[kk] = -1;
+        break;
+      }
+      const int32_t x = warp_binned_step(g, alive, t, v, k, (uint64_t)wid, J.seed, J.a_p, J.a_q, thr, sbuf, cap, lane);
+      if (mine) row[k] = alive ? x : -1;
+      if (alive) {
+        if (x < 0) {
+          alive = false;
+        } else {
+          t = v;
+          v = x;
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Traffic counter: one thread per row.
+__global__ void k_traffic(const int64_t* __restrict__ rp, int weighted, const int32_t* __restrict__ starts,
+                          int64_t n_starts, int64_t walk_begin, int64_t count, int32_t l,
+                          const int32_t* __restrict__ walks, unsigned long long* __restrict__ out2) {
+  unsigned long long steps = 0, bytes = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t* row = walks + i * (int64_t)l;
+    const int64_t s0 = starts[(walk_begin + i) % n_starts];
+    int64_t t = -1, v = s0;
+    for (int k = 0; k < l; ++k) {
+      const int32_t x = row[k];
+      if (x < 0 || v < 0) break;
+      unsigned long long b = 16 + 4ull * (unsigned long long)(rp[v + 1] - rp[v]) * (weighted ? 2 : 1) + 4;
+      if (k >= 1) b += 16 + 4ull * (unsigned long long)(rp[t + 1] - rp[t]);
+      steps += 1;
+      bytes += b;
+      t = v;
+      v = x;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    steps += __shfl_xor_sync(kFull, steps, o);
+    bytes += __shfl_xor_sync(kFull, bytes, o);
+  }
+  if ((threadIdx.x & 31) == 0 && (steps || bytes)) {
+    atomicAdd(&out2[0], steps);
+    atomicAdd(&out2[1], bytes);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launch configuration
+
+static int smem_per_block(int threads, int cap) { return (threads / 32) * cap * (int)sizeof(uint32_t); }
+
+LaunchCfg resolve_launch(const n2v_graph* g, int variant) {
+  LaunchCfg c{};
+  c.block_threads = g->tune.block_threads;
+  c.thread_max_deg = g->tune.thread_max_deg;
+  c.smem_specials = g->tune.smem_specials;
+  const int smem = smem_per_block(c.block_threads, c.smem_specials);
+  int per_sm = g->tune.blocks_per_sm;
+  if (per_sm <= 0) {
+    per_sm = 1;
+    const void* fn = variant == N2V_PERSISTENT ? (const void*)k_persistent : (const void*)k_binned_step;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, c.block_threads, smem) == cudaSuccess && occ > 0)
+      per_sm = occ;
+  }
+  c.blocks = g->sms * per_sm;
+  return c;
+}
+
+static int64_t n_chunks(const n2v_graph* g, int64_t count) {
+  const int64_t cw = g->tune.chunk_walkers;
+  if (cw <= 0 || count <= 0) return 1;
+  return (count + cw - 1) / cw;
+}
+
+struct WalkCall {
+  const int32_t* starts;
+  int64_t n_starts;
+  int32_t l;
+  uint32_t a_p, a_q;
+  uint64_t seed;
+  int64_t walk_begin, count;
+  int32_t* walks;
+  void* ws;
+  int variant;
+};
+
+// Enqueue the launches of one call on stream s.
+static cudaError_t issue(const n2v_graph* g, const WalkCall& c, cudaStream_t s) {
+  WalkJob J;
+  J.starts = c.starts;
+  J.n_starts = c.n_starts;
+  J.walk_begin = c.walk_begin;
+  J.count = c.count;
+  J.l = c.l;
+  J.a_p = c.a_p;
+  J.a_q = c.a_q;
+  J.seed = c.seed;
+  J.walks = c.walks;
+  J.status = g->status;
+  const int base = c.variant & 0xff;
+  if (base == N2V_PLAIN) {
+    const unsigned blocks = (unsigned)((c.count + 255) / 256);
+    for (int k = 0; k < c.l; ++k) k_plain_step<<<blocks, 256, 0, s>>>(g->view, J, k);
+    return cudaGetLastError();
+  }
+  const LaunchCfg L = resolve_launch(g, base);
+  const int smem = smem_per_block(L.block_threads, L.smem_specials);
+  if (base == N2V_BINNED) {
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k_binned_step, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    const int64_t warps = (c.count + 31) / 32;
+    const int wpb = L.block_threads / 32;
+    const unsigned blocks = (unsigned)((warps + wpb - 1) / wpb);
+    for (int k = 0; k < c.l; ++k)
+      k_binned_step<<<blocks, L.block_threads, smem, s>>>(g->view, J, k, L.thread_max_deg, L.smem_specials);
+    return cudaGetLastError();
+  }
+  // persistent
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  const int64_t chunks = n_chunks(g, c.count);
+  unsigned long long* counters = (unsigned long long*)c.ws;
+  cudaError_t e = cudaMemsetAsync(counters, 0, sizeof(unsigned long long) * (size_t)chunks, s);
+  if (e != cudaSuccess) return e;
+  const int64_t per = chunks == 1 ? c.count : g->tune.chunk_walkers;
+  for (int64_t ci = 0; ci < chunks; ++ci) {
+    WalkJob Jc = J;
+    const int64_t lo = ci * per;
+    Jc.walk_begin = c.walk_begin + lo;
+    Jc.count = std::min<int64_t>(per, c.count - lo);
+    Jc.walks = c.walks + lo * (int64_t)c.l;
+    k_persistent<<<L.blocks, L.block_threads, smem, s>>>(g->view, Jc, counters + ci, L.thread_max_deg, L.smem_specials);
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// CUDA-graph recording of a call's launch sequence, keyed by every argument.
+
+struct GraphEntry {
+  WalkCall key;
+  cudaGraphExec_t exec;
+};
+struct GraphCache {
+  std::mutex mu;
+  std::vector<GraphEntry> entries;
+};
+
+static bool same_call(const WalkCall& a, const WalkCall& b) { return memcmp(&a, &b, sizeof(WalkCall)) == 0; }
+
+void free_graph_cache(n2v_graph* g) {
+  GraphCache* gc = (GraphCache*)g->graph_cache;
+  if (!gc) return;
+  for (auto& e : gc->entries) cudaGraphExecDestroy(e.exec);
+  delete gc;
+  g->graph_cache = nullptr;
+}
+
+static int issue_graph(n2v_graph* g, const WalkCall& c, cudaStream_t s) {
+  if (!s) return N2V_ERR_INVALID_ARG;  // the legacy stream cannot be recorded
+  if (!g->graph_cache) g->graph_cache = new GraphCache();
+  GraphCache* gc = (GraphCache*)g->graph_cache;
+  std::lock_guard<std::mutex> lock(gc->mu);
+  for (auto& e : gc->entries)
+    if (same_call(e.key, c)) return cudaGraphLaunch(e.exec, s) == cudaSuccess ? N2V_OK : N2V_ERR_CUDA;
+  // make sure lazy function attributes are set before recording
+  if ((c.variant & 0xff) != N2V_PLAIN) resolve_launch(g, c.variant & 0xff);
+  cudaGraph_t graph = nullptr;
+  if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return N2V_ERR_CUDA;
+  cudaError_t e1 = issue(g, c, s);
+  cudaError_t e2 = cudaStreamEndCapture(s, &graph);
+  if (e1 != cudaSuccess || e2 != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return N2V_ERR_CUDA;
+  }
+  cudaGraphExec_t exec = nullptr;
+  cudaError_t e3 = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e3 != cudaSuccess) return N2V_ERR_CUDA;
+  if (gc->entries.size() >= 16) {
+    cudaGraphExecDestroy(gc->entries.front().exec);
+    gc->entries.erase(gc->entries.begin());
+  }
+  gc->entries.push_back({c, exec});
+  return cudaGraphLaunch(exec, s) == cudaSuccess ? N2V_OK : N2V_ERR_CUDA;
+}
+
+}  // namespace n2v
+
+using namespace n2v;
+
+extern "C" {
+
+int n2v_alpha_q16(double p, double q, uint32_t* a_p, uint32_t* a_q) {
+  if (!a_p || !a_q) return N2V_ERR_INVALID_ARG;
+  if (!isfinite(p) || !isfinite(q) || !(p > 0.0) || !(q > 0.0)) return N2V_ERR_INVALID_ARG;
+  // one rounding, to nearest with ties to even, of the IEEE double quotient
+  const double xp = nearbyint(65536.0 / p), xq = nearbyint(65536.0 / q);
+  if (!(xp >= 1.0 && xp <= 16777216.0 && xq >= 1.0 && xq <= 16777216.0)) return N2V_ERR_INVALID_ARG;
+  *a_p = (uint32_t)xp;
+  *a_q = (uint32_t)xq;
+  return N2V_OK;
+}
+
+int n2v_walk_ws_bytes(const n2v_graph* g, int64_t walk_count, int32_t l, int variant, size_t* bytes) {
+  if (!g || !bytes || walk_count < 0 || l < 1) return N2V_ERR_INVALID_ARG;
+  const int base = variant & 0xff;
+  if (base != N2V_PLAIN && base != N2V_BINNED && base != N2V_PERSISTENT) return N2V_ERR_INVALID_ARG;
+  size_t b = 0;
+  if (base == N2V_PERSISTENT) b = ((sizeof(unsigned long long) * (size_t)n_chunks(g, walk_count)) + 255) & ~(size_t)255;
+  *bytes = b;
+  return N2V_OK;
+}
+
+int n2v_walk(const n2v_graph* g, const int32_t* starts, int64_t n_starts, int32_t r, int32_t l, double p, double q,
+             uint64_t seed, int64_t walk_begin, int64_t walk_count, int32_t* walks, void* ws, size_t ws_bytes,
+             int variant, void* stream) {
+  if (!g || l < 1 || r < 1 || n_starts < 1 || walk_begin < 0 || walk_count < 0) return N2V_ERR_INVALID_ARG;
+  const int base = variant & 0xff;
+  if (base != N2V_PLAIN && base != N2V_BINNED && base != N2V_PERSISTENT) return N2V_ERR_INVALID_ARG;
+  if ((variant & ~0xff) & ~N2V_FLAG_CUDA_GRAPH) return N2V_ERR_INVALID_ARG;
+  if (n_starts > INT64_MAX / r) return N2V_ERR_INVALID_ARG;
+  const int64_t total = n_starts * (int64_t)r;
+  if (walk_begin > total || walk_count > total - walk_begin) return N2V_ERR_INVALID_ARG;
+  uint32_t a_p, a_q;
+  if (n2v_alpha_q16(p, q, &a_p, &a_q) != N2V_OK) return N2V_ERR_INVALID_ARG;
+  const uint64_t amax = std::max<uint64_t>(std::max<uint64_t>(a_p, a_q), kAlphaOne);
+  if (g->info.max_wsum > UINT64_MAX / amax) return N2V_ERR_OVERFLOW;
+  if (walk_count == 0) return N2V_OK;
+  if (!starts || !walks) return N2V_ERR_INVALID_ARG;
+  size_t need = 0;
+  n2v_walk_ws_bytes(g, walk_count, l, variant, &need);
+  if (need > 0 && (!ws || ws_bytes < need)) return N2V_ERR_NO_MEM;
+  if (ws && ((uintptr_t)ws & 255) != 0) return N2V_ERR_INVALID_ARG;
+  WalkCall c;
+  memset(&c, 0, sizeof(c));
+  c.starts = starts;
+  c.n_starts = n_starts;
+  c.l = l;
+  c.a_p = a_p;
+  c.a_q = a_q;
+  c.seed = seed;
+  c.walk_begin = walk_begin;
+  c.count = walk_count;
+  c.walks = walks;
+  c.ws = ws;
+  c.variant = base;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (variant & N2V_FLAG_CUDA_GRAPH) return issue_graph(const_cast<n2v_graph*>(g), c, s);
+  return issue(g, c, s) == cudaSuccess ? N2V_OK : N2V_ERR_CUDA;
+}
+
+int n2v_walk_traffic(const n2v_graph* g, const int32_t* starts, int64_t n_starts, int64_t walk_begin,
+                     int64_t walk_count, int32_t l, const int32_t* walks, uint64_t* out2, void* stream) {
+  if (!g || !out2 || l < 1 || n_starts < 1 || walk_begin < 0 || walk_count < 0) return N2V_ERR_INVALID_ARG;
+  if (walk_count > 0 && (!starts || !walks)) return N2V_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemsetAsync(out2, 0, 2 * sizeof(uint64_t), s) != cudaSuccess) return N2V_ERR_CUDA;
+  if (walk_count == 0) return N2V_OK;
+  const unsigned blocks = (unsigned)std::min<int64_t>((walk_count + 255) / 256, (int64_t)g->sms * 16);
+  k_traffic<<<blocks, 256, 0, s>>>(g->view.rp, g->weighted, starts, n_starts, walk_begin, walk_count, l, walks,
+                                   (unsigned long long*)out2);
+  return cudaGetLastError() == cudaSuccess ? N2V_OK : N2V_ERR_CUDA;
+}
+
+int n2v_stream_status(const n2v_graph* g, void* stream) {
+  if (!g) return N2V_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  uint32_t st = 0;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return N2V_ERR_CUDA;
+  if (cudaMemcpy(&st, g->status, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess) return N2V_ERR_CUDA;
+  if (st && cudaMemset(g->status, 0, sizeof(st)) != cudaSuccess) return N2V_ERR_CUDA;
+  if (st & kStTimeout) return N2V_ERR_TIMEOUT;
+  if (st & kStInternal) return N2V_ERR_CUDA;
+  if (st & kStInvalidArg) return N2V_ERR_INVALID_ARG;
+  return N2V_OK;
+}
+
+const char* n2v_strerror(int code) {
+  switch (code) {
+    case N2V_OK: return "ok";
+    case N2V_ERR_INVALID_ARG: return "invalid argument";
+    case N2V_ERR_INVALID_GRAPH: return "invalid graph (CSR not canonical)";
+    case N2V_ERR_OVERFLOW: return "weighted totals could overflow 64 bits for these p, q";
+    case N2V_ERR_NO_MEM: return "caller buffer too small";
+    case N2V_ERR_TIMEOUT: return "bounded device wait timed out";
+    case N2V_ERR_CUDA: return "CUDA runtime error";
+    default: return "unknown status";
+  }
+}
+
+int n2v_launch_shape(const n2v_graph* g, int32_t* sms, int32_t* blocks, int32_t* threads) {
+  if (!g) return N2V_ERR_INVALID_ARG;
+  LaunchCfg L = resolve_launch(g, N2V_PERSISTENT);
+  if (sms) *sms = g->sms;
+  if (blocks) *blocks = L.blocks;
+  if (threads) *threads = L.block_threads;
+  return N2V_OK;
+}
+
+}  // extern "C"

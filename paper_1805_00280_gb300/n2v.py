@@ -1,0 +1,279 @@
+"""Python binding of the C ABI in include/n2v.h (argument marshalling only).
+
+Every function named ``n2v_*`` here calls the C entry point of the same name
+in the in-tree ``lib/libn2v.so``; tensors are passed as raw device pointers
+and streams as ``cudaStream_t`` handles.  PyTorch only supplies device memory
+and streams.  There is no CPU or PyTorch fallback: if the CUDA library is
+missing, importing this module raises.
+
+``Graph`` and ``walk`` are conveniences that allocate the caller-owned buffers
+with torch and then call the same entry points.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+from . import _build
+
+N2V_OK = 0
+N2V_ERR_INVALID_ARG = -1
+N2V_ERR_INVALID_GRAPH = -2
+N2V_ERR_OVERFLOW = -3
+N2V_ERR_NO_MEM = -4
+N2V_ERR_TIMEOUT = -5
+N2V_ERR_CUDA = -6
+
+N2V_PLAIN = 0
+N2V_BINNED = 1
+N2V_PERSISTENT = 2
+N2V_FLAG_CUDA_GRAPH = 0x100
+
+VARIANTS = {"plain": N2V_PLAIN, "binned": N2V_BINNED, "persistent": N2V_PERSISTENT}
+
+
+class N2VError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        super().__init__(f"{what}: {n2v_strerror(code)} ({code})" if what else f"{n2v_strerror(code)} ({code})")
+
+
+class n2v_tune(ctypes.Structure):
+    _fields_ = [("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("thread_max_deg", ctypes.c_int32), ("smem_specials", ctypes.c_int32),
+                ("hub_count", ctypes.c_int32), ("hub_min_degree", ctypes.c_int32),
+                ("chunk_walkers", ctypes.c_int32), ("hub_budget_mb", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 8)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+class n2v_graph_info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("weighted", ctypes.c_int32),
+                ("hub_count", ctypes.c_int32), ("max_degree", ctypes.c_int64), ("max_wsum", ctypes.c_uint64),
+                ("hub_min_degree", ctypes.c_int64), ("hub_slots", ctypes.c_int64),
+                ("deg_hist", ctypes.c_int64 * 34)]
+
+
+_LIB = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libn2v.so (building it in-tree when its sources changed)."""
+    global _LIB
+    if _LIB is None:
+        path = _build.LIBN2V
+        if not os.path.exists(path) or os.environ.get("N2V_NO_AUTOBUILD") != "1":
+            path = _build.build_n2v()
+        L = ctypes.CDLL(path)
+        vp, i64, i32, u64, dbl, sz = (ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64,
+                                      ctypes.c_double, ctypes.c_size_t)
+        P = ctypes.POINTER
+        L.n2v_tune_default.argtypes = [P(n2v_tune)]
+        L.n2v_tune_default.restype = None
+        L.n2v_alpha_q16.argtypes = [dbl, dbl, P(ctypes.c_uint32), P(ctypes.c_uint32)]
+        L.n2v_graph_aux_bytes.argtypes = [i64, i64, ctypes.c_int, P(n2v_tune), P(sz)]
+        L.n2v_graph_load.argtypes = [vp, vp, vp, i64, i64, vp, sz, P(n2v_tune), vp, P(vp)]
+        L.n2v_graph_info_get.argtypes = [vp, P(n2v_graph_info)]
+        L.n2v_graph_retune.argtypes = [vp, P(n2v_tune), vp]
+        L.n2v_graph_free.argtypes = [vp]
+        L.n2v_graph_free.restype = None
+        L.n2v_walk_ws_bytes.argtypes = [vp, i64, i32, ctypes.c_int, P(sz)]
+        L.n2v_walk.argtypes = [vp, vp, i64, i32, i32, dbl, dbl, u64, i64, i64, vp, vp, sz, ctypes.c_int, vp]
+        L.n2v_walk_traffic.argtypes = [vp, vp, i64, i64, i64, i32, vp, vp, vp]
+        L.n2v_stream_status.argtypes = [vp, vp]
+        L.n2v_strerror.argtypes = [ctypes.c_int]
+        L.n2v_strerror.restype = ctypes.c_char_p
+        L.n2v_launch_shape.argtypes = [vp, P(i32), P(i32), P(i32)]
+        _LIB = L
+    return _LIB
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _check(rc: int, what: str) -> None:
+    if rc != N2V_OK:
+        raise N2VError(rc, what)
+
+
+# --------------------------------------------------------------------------
+# 1:1 entry points
+
+def n2v_strerror(code: int) -> str:
+    return lib().n2v_strerror(code).decode()
+
+
+def n2v_tune_default() -> n2v_tune:
+    t = n2v_tune()
+    lib().n2v_tune_default(ctypes.byref(t))
+    return t
+
+
+def n2v_alpha_q16(p: float, q: float) -> tuple[int, int]:
+    ap, aq = ctypes.c_uint32(), ctypes.c_uint32()
+    _check(lib().n2v_alpha_q16(p, q, ctypes.byref(ap), ctypes.byref(aq)), "n2v_alpha_q16")
+    return ap.value, aq.value
+
+
+def n2v_graph_aux_bytes(n: int, nnz: int, weighted: bool, tune: n2v_tune | None = None) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().n2v_graph_aux_bytes(n, nnz, int(weighted), ctypes.byref(tune) if tune else None,
+                                     ctypes.byref(b)), "n2v_graph_aux_bytes")
+    return b.value
+
+
+def n2v_graph_load(row_ptr, col, w, n: int, nnz: int, aux, tune: n2v_tune | None = None, stream=None) -> int:
+    h = ctypes.c_void_p()
+    aux_bytes = aux.numel() * aux.element_size()
+    rc = lib().n2v_graph_load(_ptr(row_ptr), _ptr(col), _ptr(w), n, nnz, _ptr(aux), aux_bytes,
+                              ctypes.byref(tune) if tune else None, _stream(stream), ctypes.byref(h))
+    _check(rc, "n2v_graph_load")
+    return h.value
+
+
+def n2v_graph_info_get(handle: int) -> n2v_graph_info:
+    info = n2v_graph_info()
+    _check(lib().n2v_graph_info_get(handle, ctypes.byref(info)), "n2v_graph_info_get")
+    return info
+
+
+def n2v_graph_retune(handle: int, tune: n2v_tune, stream=None) -> None:
+    _check(lib().n2v_graph_retune(handle, ctypes.byref(tune), _stream(stream)), "n2v_graph_retune")
+
+
+def n2v_graph_free(handle: int) -> None:
+    lib().n2v_graph_free(handle)
+
+
+def n2v_walk_ws_bytes(handle: int, walk_count: int, l: int, variant: int) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().n2v_walk_ws_bytes(handle, walk_count, l, variant, ctypes.byref(b)), "n2v_walk_ws_bytes")
+    return b.value
+
+
+def n2v_walk(handle: int, starts, n_starts: int, r: int, l: int, p: float, q: float, seed: int,
+             walk_begin: int, walk_count: int, walks, ws, variant: int, stream=None) -> None:
+    ws_bytes = 0 if ws is None else ws.numel() * ws.element_size()
+    rc = lib().n2v_walk(handle, _ptr(starts), n_starts, r, l, p, q, seed, walk_begin, walk_count, _ptr(walks),
+                        _ptr(ws), ws_bytes, variant, _stream(stream))
+    _check(rc, "n2v_walk")
+
+
+def n2v_walk_traffic(handle: int, starts, n_starts: int, walk_begin: int, walk_count: int, l: int, walks,
+                     out2, stream=None) -> None:
+    _check(lib().n2v_walk_traffic(handle, _ptr(starts), n_starts, walk_begin, walk_count, l, _ptr(walks),
+                                  _ptr(out2), _stream(stream)), "n2v_walk_traffic")
+
+
+def n2v_stream_status(handle: int, stream=None) -> int:
+    return int(lib().n2v_stream_status(handle, _stream(stream)))
+
+
+def n2v_launch_shape(handle: int) -> tuple[int, int, int]:
+    a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().n2v_launch_shape(handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "n2v_launch_shape")
+    return a.value, b.value, c.value
+
+
+# --------------------------------------------------------------------------
+# conveniences
+
+def default_tune(**kw) -> n2v_tune:
+    t = n2v_tune_default()
+    for k, v in kw.items():
+        setattr(t, k, int(v))
+    return t
+
+
+class Graph:
+    """A device-resident CSR graph: owns the torch tensors and the aux buffer."""
+
+    def __init__(self, row_ptr, col, w=None, tune: n2v_tune | None = None, device="cuda", stream=None):
+        self.row_ptr = torch.as_tensor(row_ptr, dtype=torch.int64).to(device).contiguous()
+        self.col = torch.as_tensor(col, dtype=torch.int32).to(device).contiguous()
+        if w is not None:
+            if isinstance(w, np.ndarray):
+                w = torch.from_numpy(np.ascontiguousarray(w).view(np.int32))
+            elif w.dtype != torch.int32:
+                w = w.view(torch.int32)  # uint32 bits, unchanged
+            w = w.to(device).contiguous()
+        self.w = w
+        self.n = int(self.row_ptr.numel() - 1)
+        self.nnz = int(self.col.numel())
+        self.tune = tune if tune is not None else n2v_tune_default()
+        nbytes = n2v_graph_aux_bytes(self.n, self.nnz, self.w is not None, self.tune)
+        self.aux = torch.empty(max(nbytes, 256) // 8 + 32, dtype=torch.int64, device=device)
+        self.handle = n2v_graph_load(self.row_ptr, self.col, self.w, self.n, self.nnz, self.aux, self.tune,
+                                     stream)
+
+    @classmethod
+    def from_csr(cls, csr, tune: n2v_tune | None = None, device="cuda", stream=None) -> "Graph":
+        return cls(torch.from_numpy(csr.row_ptr), torch.from_numpy(csr.col), csr.w, tune, device, stream)
+
+    def info(self) -> n2v_graph_info:
+        return n2v_graph_info_get(self.handle)
+
+    def retune(self, tune: n2v_tune, stream=None) -> None:
+        n2v_graph_retune(self.handle, tune, stream)
+        self.tune = tune
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            n2v_graph_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def walk(graph: Graph, starts, r: int, l: int, p: float, q: float, seed: int, variant: str | int = "persistent",
+         walk_begin: int = 0, walk_count: int | None = None, out=None, ws=None, stream=None,
+         cuda_graph: bool = False) -> torch.Tensor:
+    """Allocate (if needed) and fill int32 walks [walk_count, l] on the graph's device."""
+    dev = graph.row_ptr.device
+    starts = torch.as_tensor(starts, dtype=torch.int32).to(dev).contiguous()
+    n_starts = int(starts.numel())
+    if walk_count is None:
+        walk_count = n_starts * r - walk_begin
+    v = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+    if cuda_graph:
+        v |= N2V_FLAG_CUDA_GRAPH
+    if out is None:
+        out = torch.empty((walk_count, l), dtype=torch.int32, device=dev)
+    need = n2v_walk_ws_bytes(graph.handle, walk_count, l, v)
+    if need and (ws is None or ws.numel() * ws.element_size() < need):
+        ws = torch.empty(need // 8 + 32, dtype=torch.int64, device=dev)
+    n2v_walk(graph.handle, starts, n_starts, r, l, p, q, seed, walk_begin, walk_count, out, ws, v, stream)
+    return out
+
+
+def traffic(graph: Graph, starts, walk_begin: int, walks: torch.Tensor, stream=None) -> tuple[int, int]:
+    """(real transitions, model adjacency bytes) of the rows in ``walks`` (synchronises)."""
+    dev = graph.row_ptr.device
+    starts = torch.as_tensor(starts, dtype=torch.int32).to(dev).contiguous()
+    out2 = torch.zeros(2, dtype=torch.int64, device=dev)
+    n2v_walk_traffic(graph.handle, starts, int(starts.numel()), walk_begin, int(walks.shape[0]),
+                     int(walks.shape[1]), walks, out2, stream)
+    o = out2.cpu()
+    return int(o[0]), int(o[1])

@@ -1,0 +1,265 @@
+"""GPU sampler vs CPU oracle: bit-exact walks through the C ABI (needs a GB300).
+
+Walks are integer results (vertex ids chosen by integer prefix sums under a
+fixed Philox stream), so the bar is bit-exact equality of every compared row.
+Every variant (plain, binned, persistent, persistent recorded as a CUDA graph)
+and every tuning that changes which code path runs (thread vs warp bins, the
+shared-memory spill path, the hub hash sets, chunked launches) must give the
+oracle's rows.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1805_00280_gb300 import graphs as G
+from paper_1805_00280_gb300 import n2v
+from small_graphs import big_star, small_graphs, two_hubs
+
+pytestmark = pytest.mark.gpu
+
+VARIANTS = ["plain", "binned", "persistent"]
+
+TUNES = {
+    "default": {},
+    "all_warp": dict(thread_max_deg=0),
+    "all_thread": dict(thread_max_deg=1 << 30),
+    "spill": dict(thread_max_deg=0, smem_specials=32),
+    "hubs": dict(thread_max_deg=0, hub_count=4096, hub_min_degree=2),
+    "chunks": dict(chunk_walkers=1000, block_threads=128),
+}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("CUDA device required")
+    n2v.lib()
+    yield
+    torch.cuda.synchronize()
+
+
+def gpu_rows(g, starts, r, l, p, q, seed, variant, tune=None, walk_begin=0, walk_count=None, cuda_graph=False,
+             graph=None):
+    G_ = graph if graph is not None else n2v.Graph.from_csr(g, tune=n2v.default_tune(**(tune or {})))
+    out = n2v.walk(G_, starts, r, l, p, q, seed, variant, walk_begin=walk_begin, walk_count=walk_count,
+                   cuda_graph=cuda_graph)
+    assert n2v.n2v_stream_status(G_.handle) == n2v.N2V_OK
+    return out.cpu().numpy()
+
+
+def oracle_rows(g, starts, l, p, q, seed, ids, threads=8):
+    return oracle.walk(g.row_ptr, g.col, g.w, np.asarray(starts, np.int32), l, p, q, seed,
+                       np.asarray(ids, np.int64), threads=threads)
+
+
+# --------------------------------------------------------------------------
+# small graphs: every variant x every tuning, full rows
+
+SMALL = small_graphs()
+SMALL_CASES = [(nm, pq) for nm in SMALL for pq in [(1.0, 1.0), (0.25, 4.0), (4.0, 0.25), (3.0, 0.7)]]
+
+
+@pytest.mark.parametrize("name,pq", SMALL_CASES, ids=[f"{a}-{b[0]}-{b[1]}" for a, b in SMALL_CASES])
+def test_small_graphs_every_variant_and_tuning(name, pq):
+    g = SMALL[name]
+    p, q = pq
+    starts = np.arange(g.n, dtype=np.int32)
+    r, l = 37, 9  # walk count not a multiple of 32
+    want = oracle_rows(g, starts, l, p, q, 5, np.arange(g.n * r))
+    for tname, tune in TUNES.items():
+        graph = n2v.Graph.from_csr(g, tune=n2v.default_tune(**tune))
+        for v in VARIANTS:
+            got = gpu_rows(g, starts, r, l, p, q, 5, v, graph=graph)
+            np.testing.assert_array_equal(got, want, err_msg=f"{name} {tname} {v}")
+
+
+# --------------------------------------------------------------------------
+# the Erdos-Renyi workload: G(n=1e4, m=1e5), r=10, l=80, p=0.5, q=2, full output
+
+@pytest.fixture(scope="module")
+def er():
+    wl = G.WORKLOADS["er"]
+    g = G.workload_graph("er")
+    starts = np.arange(g.n, dtype=np.int32)
+    p, q = wl.pq[0]
+    want = oracle_rows(g, starts, wl.l, p, q, wl.seed, np.arange(g.n * wl.r))
+    return g, starts, wl, want
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_er_full_output(er, variant):
+    g, starts, wl, want = er
+    p, q = wl.pq[0]
+    got = gpu_rows(g, starts, wl.r, wl.l, p, q, wl.seed, variant)
+    np.testing.assert_array_equal(got, want)
+
+
+def test_er_cuda_graph_replay(er):
+    g, starts, wl, want = er
+    p, q = wl.pq[0]
+    graph = n2v.Graph.from_csr(g)
+    for _ in range(2):  # record, then replay
+        got = gpu_rows(g, starts, wl.r, wl.l, p, q, wl.seed, "persistent", cuda_graph=True, graph=graph)
+        np.testing.assert_array_equal(got, want)
+    got = gpu_rows(g, starts, wl.r, wl.l, p, q, wl.seed, "plain", cuda_graph=True, graph=graph)
+    np.testing.assert_array_equal(got, want)
+
+
+def test_er_traffic_matches_oracle(er):
+    g, starts, wl, want = er
+    graph = n2v.Graph.from_csr(g)
+    walks = torch.from_numpy(want).cuda()
+    assert n2v.traffic(graph, starts, 0, walks) == oracle.traffic(g.row_ptr, False, starts,
+                                                                  np.arange(want.shape[0]), want)
+
+
+def test_split_ranges_equal_whole(er):
+    """Any split of the walk-id range (chunking, sharding) gives the same rows."""
+    g, starts, wl, want = er
+    p, q = wl.pq[0]
+    graph = n2v.Graph.from_csr(g)
+    total = g.n * wl.r
+    cuts = [0, 1, 33, 40_000, 77_777, total]
+    for v in VARIANTS:
+        parts = [gpu_rows(g, starts, wl.r, wl.l, p, q, wl.seed, v, walk_begin=a, walk_count=b - a, graph=graph)
+                 for a, b in zip(cuts[:-1], cuts[1:])]
+        np.testing.assert_array_equal(np.concatenate(parts), want)
+
+
+# --------------------------------------------------------------------------
+# R-MAT graphs
+
+@pytest.mark.parametrize("weighted", [False, True])
+@pytest.mark.parametrize("pq", [(1.0, 1.0), (0.25, 4.0), (4.0, 0.25)])
+def test_rmat14_full_output(weighted, pq):
+    g = G.rmat(14, 16, 0.57, 0.19, 0.19, 3)
+    if weighted:
+        g = G.with_weights(g, 9, 1, 100)
+    p, q = pq
+    starts = np.arange(g.n, dtype=np.int32)
+    want = oracle_rows(g, starts, 20, p, q, 77, np.arange(g.n * 2))
+    for tname in ["default", "hubs", "spill"]:
+        graph = n2v.Graph.from_csr(g, tune=n2v.default_tune(**TUNES[tname]))
+        for v in VARIANTS:
+            got = gpu_rows(g, starts, 2, 20, p, q, 77, v, graph=graph)
+            np.testing.assert_array_equal(got, want, err_msg=f"{tname} {v}")
+
+
+def sample_ids(g, n_starts, r, k, seed):
+    """k random walk ids plus every walk that starts at one of the 64 largest hubs."""
+    rng = np.random.default_rng(seed)
+    ids = rng.choice(n_starts * r, size=min(k, n_starts * r), replace=False)
+    hubs = np.argsort(-g.degrees())[:64]
+    hub_ids = (np.arange(r)[:, None] * n_starts + hubs[None, :]).ravel()
+    return np.unique(np.concatenate([ids, hub_ids]))
+
+
+@pytest.fixture(scope="module")
+def rmat20():
+    g = G.workload_graph("rmat20")
+    return g, n2v.Graph.from_csr(g, tune=n2v.default_tune(hub_count=1024))
+
+
+@pytest.mark.parametrize("pq", [(1.0, 1.0), (0.25, 4.0), (4.0, 0.25)])
+def test_rmat20_workload(rmat20, pq):
+    """R-MAT scale 20 at full size: every variant agrees on the whole output, and
+    sampled rows (random ids + walks from the largest hubs) match the oracle."""
+    g, graph = rmat20
+    wl = G.WORKLOADS["rmat20"]
+    p, q = pq
+    starts = np.arange(g.n, dtype=np.int32)
+    outs = {v: n2v.walk(graph, starts, wl.r, wl.l, p, q, wl.seed, v) for v in VARIANTS}
+    assert n2v.n2v_stream_status(graph.handle) == n2v.N2V_OK
+    for v in VARIANTS[:-1]:
+        assert torch.equal(outs[v], outs["persistent"]), v
+    ids = sample_ids(g, g.n, wl.r, 3000, 1)
+    want = oracle_rows(g, starts, wl.l, p, q, wl.seed, ids)
+    got = outs["persistent"][torch.from_numpy(ids).cuda()].cpu().numpy()
+    np.testing.assert_array_equal(got, want)
+
+
+def test_rmat23_weighted_workload():
+    """Weighted R-MAT scale 23 (w in [1,100]), p=1, q=0.5, persistent sampler with
+    the hub cache on the top 0.1% of vertices: sampled rows match the oracle."""
+    wl = G.WORKLOADS["rmat23w"]
+    g = G.workload_graph("rmat23w")
+    graph = n2v.Graph.from_csr(g, tune=n2v.default_tune(hub_count=g.n // 1000))
+    assert graph.info().hub_count > 0
+    p, q = wl.pq[0]
+    starts = np.arange(g.n, dtype=np.int32)
+    out = n2v.walk(graph, starts, wl.r, wl.l, p, q, wl.seed, "persistent")
+    assert n2v.n2v_stream_status(graph.handle) == n2v.N2V_OK
+    ids = sample_ids(g, g.n, wl.r, 1500, 2)
+    want = oracle_rows(g, starts, wl.l, p, q, wl.seed, ids)
+    got = out[torch.from_numpy(ids).cuda()].cpu().numpy()
+    np.testing.assert_array_equal(got, want)
+
+
+# --------------------------------------------------------------------------
+# degenerate and extreme shapes
+
+def test_long_lists_star_and_twin_hubs():
+    for g in [big_star(1 << 18), two_hubs(3000, extra=50)]:
+        starts = np.arange(min(g.n, 4000), dtype=np.int32)
+        want = oracle_rows(g, starts, 5, 0.5, 2.0, 3, np.arange(starts.size))
+        for tname in ["default", "hubs", "spill"]:
+            graph = n2v.Graph.from_csr(g, tune=n2v.default_tune(**TUNES[tname]))
+            for v in VARIANTS:
+                got = gpu_rows(g, starts, 1, 5, 0.5, 2.0, 3, v, graph=graph)
+                np.testing.assert_array_equal(got, want, err_msg=f"{g.name} {tname} {v}")
+
+
+def test_isolated_starts_and_l1():
+    g = G.from_edges(6, [(0, 1), (1, 2)])  # 3, 4, 5 isolated
+    starts = np.arange(6, dtype=np.int32)
+    for l in (1, 3):
+        want = oracle_rows(g, starts, l, 2.0, 0.5, 1, np.arange(12))
+        for v in VARIANTS:
+            np.testing.assert_array_equal(gpu_rows(g, starts, 2, l, 2.0, 0.5, 1, v), want)
+    assert (want[3:6] == -1).all()
+
+
+def test_empty_call_is_a_no_op():
+    g = SMALL["und7"]
+    graph = n2v.Graph.from_csr(g)
+    out = torch.full((0, 4), 7, dtype=torch.int32, device="cuda")
+    for v in VARIANTS:
+        n2v.walk(graph, [0], 1, 4, 1.0, 1.0, 1, v, walk_begin=0, walk_count=0, out=out)
+    assert n2v.n2v_stream_status(graph.handle) == n2v.N2V_OK
+
+
+def test_start_out_of_range_sets_status():
+    g = SMALL["und7"]
+    graph = n2v.Graph.from_csr(g)
+    for v in VARIANTS:
+        out = n2v.walk(graph, [0, 99], 1, 4, 1.0, 1.0, 1, v)
+        assert n2v.n2v_stream_status(graph.handle) == n2v.N2V_ERR_INVALID_ARG
+        assert (out[1] == -1).all().item()
+        assert n2v.n2v_stream_status(graph.handle) == n2v.N2V_OK  # cleared
+
+
+def test_overflow_is_rejected():
+    g = G.from_edges(301, [(0, i) for i in range(1, 301)], weights=[2**32 - 1] * 300)
+    graph = n2v.Graph.from_csr(g)
+    n2v.walk(graph, [1], 1, 3, 1.0, 1.0, 1, "persistent")  # max_wsum * 2^16 < 2^64
+    with pytest.raises(n2v.N2VError) as e:
+        n2v.walk(graph, [1], 1, 3, 2.0**-8, 1.0, 1, "persistent")
+    assert e.value.code == n2v.N2V_ERR_OVERFLOW
+
+
+@pytest.mark.parametrize("bad", ["unsorted", "duplicate", "out_of_range", "row_ptr"])
+def test_invalid_graph_is_rejected(bad):
+    g = SMALL["und7"]
+    rp, col = g.row_ptr.copy(), g.col.copy()
+    if bad == "unsorted":
+        col[0], col[1] = col[1], col[0]
+    elif bad == "duplicate":
+        col[1] = col[0]
+    elif bad == "out_of_range":
+        col[3] = 7
+    else:
+        rp[2], rp[3] = rp[3], rp[2]
+    with pytest.raises(n2v.N2VError) as e:
+        n2v.Graph(rp, col)
+    assert e.value.code == n2v.N2V_ERR_INVALID_GRAPH

@@ -22,6 +22,7 @@ import pytest
 
 import oracle
 from paper_1805_00280_gb300 import graphs as G
+from small_graphs import small_graphs
 
 scipy_stats = pytest.importorskip("scipy.stats")
 
@@ -103,29 +104,6 @@ def run(g, starts, l, p, q, seed, ids, alpha=None):
 
 # --------------------------------------------------------------------------
 # small graphs for enumeration
-
-def small_graphs():
-    rng = np.random.default_rng(2024)
-    out = {}
-    # a 7-vertex undirected graph with triangles, a pendant vertex and a square
-    e1 = [(0, 1), (0, 2), (1, 2), (1, 3), (2, 3), (3, 4), (4, 5), (5, 6), (6, 3), (2, 5), (0, 6)]
-    out["und7"] = G.from_edges(7, e1)
-    out["und7w"] = G.from_edges(7, e1, weights=list(rng.integers(1, 10, len(e1))))
-    # K5 with weights (every non-return neighbour is a common neighbour)
-    k5 = [(i, j) for i in range(5) for j in range(i + 1, 5)]
-    out["k5w"] = G.from_edges(5, k5, weights=list(rng.integers(1, 6, len(k5))))
-    # directed, with a sink (vertex 5), a self-loop at 1 and an asymmetric pair
-    d = [(0, 1), (1, 1), (1, 2), (2, 0), (2, 3), (3, 1), (3, 4), (4, 2), (4, 5), (0, 3), (1, 4)]
-    out["dir6"] = G.from_edges(6, d, symmetric=False)
-    # directed weighted with a zero-weight edge (never chosen)
-    dw = [(0, 1), (1, 0), (1, 2), (2, 1), (2, 0), (0, 2), (2, 3), (3, 2), (1, 3)]
-    out["dir4w0"] = G.from_edges(4, dw, weights=[3, 1, 0, 2, 5, 1, 4, 2, 1], symmetric=False)
-    # random graph on 8 vertices
-    pairs = [(i, j) for i in range(8) for j in range(i + 1, 8)]
-    pick = rng.choice(len(pairs), 14, replace=False)
-    out["rand8"] = G.from_edges(8, [pairs[i] for i in sorted(pick)])
-    return out
-
 
 SMALL = small_graphs()
 PQ = [(1.0, 1.0), (0.25, 4.0), (4.0, 0.25), (0.5, 2.0), (3.0, 0.7)]
