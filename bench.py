@@ -51,6 +51,9 @@ def parse_args():
     ap.add_argument("--tune", default="", help="JSON dict of n2v_tune fields")
     ap.add_argument("--pq", default="", help="override (p,q) list, e.g. '1,1;0.25,4'")
     ap.add_argument("--r", type=int, default=0, help="override walks per vertex")
+    ap.add_argument("--walk-count", type=int, default=0, help="limit walks per launch (profiling cases)")
+    ap.add_argument("--compare-rounds", type=int, default=1,
+                    help="the compared variants run the first R rounds (every start vertex R times)")
     return ap.parse_args()
 
 
@@ -253,8 +256,6 @@ def run_ours(args):
     g = G.workload_graph(wl.name)
     gen_s = time.perf_counter() - t0
     tune = n2v.default_tune(**(json.loads(args.tune) if args.tune else {}))
-    if "hub_count" not in (json.loads(args.tune) if args.tune else {}):
-        tune.hub_count = max(64, g.n // 1000)  # top 0.1% of vertices by degree
     t0 = time.perf_counter()
     graph = n2v.Graph.from_csr(g, tune=tune, device=dev)
     load_s = time.perf_counter() - t0
@@ -262,6 +263,8 @@ def run_ours(args):
     l = wl.l
     n_start = g.n
     W = n_start * r                       # walks per rank
+    if args.walk_count:
+        W = min(W, args.walk_count)
     r_total = r * world                   # rank k runs rounds [k r, (k+1) r)
     walk_begin = rank * W
     starts = torch.arange(n_start, dtype=torch.int32, device=dev)
@@ -333,29 +336,38 @@ def run_ours(args):
                 "kernel": {"persistent": "k_persistent", "binned": "k_binned_step", "plain": "k_plain_step"}[args.variant],
                 "bytes_model": "16 + 4 deg(v) (1+weighted) + [k>=1](16 + 4 deg(t)) + 4 per real transition"}
 
-    # ---- the other variants, once each, and their agreement with the main one
+    # ---- the other variants, once each on the first rounds of walk ids (every start vertex
+    #      `compare_rounds` times), beside the main variant on the same rows
     compare = {}
-    for vname in [v for v in args.compare.split(",") if v and v != args.variant]:
-        vcode = n2v.VARIANTS[vname]
-        tmp = torch.empty((W, l), dtype=torch.int32, device=dev)
-        ms, same = [], True
-        for i in range(len(pq)):
-            launch(i, vcode, tmp)  # warm-up (also fills tmp)
-            torch.cuda.synchronize(dev)
-            flush.fill_(7)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            launch(i, vcode, tmp)
-            b.record(stream)
-            torch.cuda.synchronize(dev)
-            ms.append(a.elapsed_time(b))
-            same &= bool(torch.equal(tmp, outs[i]))
+    Wc = min(W, n_start * max(1, args.compare_rounds))
+    names = [v for v in args.compare.split(",") if v and v != args.variant]
+    if names:
+        tmp = torch.empty((Wc, l), dtype=torch.int32, device=dev)
+        sub = {}
+        for vname in [args.variant] + names:
+            vcode = n2v.VARIANTS[vname]
+            ms, same, tr = [], True, 0
+            for i in range(len(pq)):
+                launch_sub = lambda: n2v.n2v_walk(graph.handle, starts, n_start, r_total, l, pq[i][0], pq[i][1],
+                                                  wl.seed, walk_begin, Wc, tmp, ws, vcode, stream)
+                launch_sub()  # warm-up
+                torch.cuda.synchronize(dev)
+                flush.fill_(7)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                launch_sub()
+                b.record(stream)
+                torch.cuda.synchronize(dev)
+                ms.append(a.elapsed_time(b))
+                same &= bool(torch.equal(tmp, outs[i][:Wc]))
+                tr += n2v.traffic(graph, starts, walk_begin, tmp)[0]
+            sub[vname] = {"value": tr * world / (sum(ms) / 1e3), "unit": UNIT, "ms": sum(ms),
+                          "bit_identical_to_timed_" + args.variant: same,
+                          "launches": len(pq) * (l if vname != "persistent" else 1)}
         del tmp
-        compare[vname] = {"value": sum(trans) * world / (sum(ms) / 1e3), "unit": UNIT, "ms_per_step": sum(ms),
-                          "bit_identical_to_" + args.variant: same,
-                          "launches_per_step": len(pq) * (l if vname != "persistent" else 1)}
-    if compare.get("plain"):
-        compare["speedup_over_plain"] = value / compare["plain"]["value"]
+        compare = {"walks_per_pq": Wc, "variants": sub}
+        if "plain" in sub:
+            compare["speedup_over_plain_same_rows"] = sub[args.variant]["value"] / sub["plain"]["value"]
 
     # ---- end to end through the C ABI with host buffers
     e2e = None

@@ -88,7 +88,10 @@ typedef struct n2v_tune {
   int32_t hub_min_degree;  /* a vertex needs at least this degree to get a hashed set         */
   int32_t chunk_walkers;   /* walkers per persistent launch (0 = all in one launch)           */
   int32_t hub_budget_mb;   /* MiB of device memory for all hub hash sets (8 bytes per slot)   */
-  int32_t reserved[8];     /* must be zero                                                    */
+  int32_t hash_cap;        /* entries of the per-warp shared-memory hash of the shorter list   */
+  int32_t stream_ratio;    /* x10: stream the longer list when its length is at most
+                              stream_ratio/10 * 32*ceil(short/32) * log2(long) (else probe it) */
+  int32_t reserved[6];     /* must be zero                                                    */
 } n2v_tune;
 
 /* Fill *t with the library defaults. */

@@ -220,7 +220,10 @@ static bool tune_ok(const n2v_tune& t) {
   if (t.block_threads < 64 || t.block_threads > 1024 || t.block_threads % 32) return false;
   if (t.blocks_per_sm < 0 || t.thread_max_deg < 0 || t.smem_specials < 32 || t.smem_specials > 8192) return false;
   if (t.hub_count < 0 || t.hub_min_degree < 0 || t.chunk_walkers < 0 || t.hub_budget_mb < 0) return false;
-  for (int i = 0; i < 8; ++i)
+  if (t.hash_cap < 32 || t.hash_cap > 4096 || (t.hash_cap & (t.hash_cap - 1)) || t.stream_ratio < 0 ||
+      t.stream_ratio > 1000000)
+    return false;
+  for (int i = 0; i < 6; ++i)
     if (t.reserved[i]) return false;
   return true;
 }
@@ -242,6 +245,8 @@ void n2v_tune_default(n2v_tune* t) {
   t->hub_min_degree = 256;
   t->chunk_walkers = 0;
   t->hub_budget_mb = 1024;
+  t->hash_cap = 512;
+  t->stream_ratio = 40;
 }
 
 int n2v_graph_aux_bytes(int64_t n, int64_t nnz, int weighted, const n2v_tune* t, size_t* bytes) {

@@ -52,7 +52,15 @@ struct LaunchCfg {
   int blocks;
   int thread_max_deg;
   int smem_specials;  // per warp
+  int hash_cap;       // per warp: entries of the shared-memory hash (2x slots)
+  int stream_ratio;   // x10
 };
+
+// Shared memory of one warp: the hash table (2 * hash_cap int2 slots), then
+// the specials buffer (smem_specials uint32), rounded to 16 bytes.
+__host__ __device__ __forceinline__ int warp_smem_bytes(const LaunchCfg& c) {
+  return (2 * c.hash_cap * 8 + c.smem_specials * 4 + 15) & ~15;
+}
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of the

@@ -45,10 +45,10 @@ __global__ void __launch_bounds__(256) k_plain_step(GraphView g, WalkJob J, int 
 // ---------------------------------------------------------------------------
 // Binned: one launch per step k; warp w owns walkers [32w, 32w + 32) and bins
 // each of their steps by degree (own lane, or the whole warp).
-__global__ void k_binned_step(GraphView g, WalkJob J, int k, int thr, int cap) {
-  extern __shared__ uint32_t smem[];
+__global__ void k_binned_step(GraphView g, WalkJob J, int k, LaunchCfg L) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t* sbuf = smem + warp * cap;
+  const WarpSmem sm = warp_smem(smem_raw, warp, L);
   const int64_t base = ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * 32;
   if (base >= J.count) return;  // uniform per warp
   const int64_t i = base + lane;
@@ -72,7 +72,8 @@ __global__ void k_binned_step(GraphView g, WalkJob J, int k, int thr, int cap) {
       atomicOr(J.status, kStInvalidArg);
     }
   }
-  const int32_t x = warp_binned_step(g, alive, t, v, k, (uint64_t)wid, J.seed, J.a_p, J.a_q, thr, sbuf, cap, lane);
+  const int32_t x = warp_binned_step(g, alive, t, v, k, (uint64_t)wid, J.seed, J.a_p, J.a_q, L.thread_max_deg, sm,
+                                     L.stream_ratio, lane);
   if (mine) row[k] = alive ? x : -1;
 }
 
@@ -81,10 +82,10 @@ __global__ void k_binned_step(GraphView g, WalkJob J, int k, int thr, int cap) {
 // time from a device counter and runs them to the end; every step is binned
 // by degree as above.  Walkers are independent (FN-Multi's observation,
 // Section 3.4), so the order in which warps take them does not change any row.
-__global__ void k_persistent(GraphView g, WalkJob J, unsigned long long* __restrict__ counter, int thr, int cap) {
-  extern __shared__ uint32_t smem[];
+__global__ void k_persistent(GraphView g, WalkJob J, unsigned long long* __restrict__ counter, LaunchCfg L) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t* sbuf = smem + warp * cap;
+  const WarpSmem sm = warp_smem(smem_raw, warp, L);
   for (;;) {
     unsigned long long base = 0;
     if (lane == 0) base = atomicAdd(counter, 32ull);
@@ -111,7 +112,8 @@ __global__ void k_persistent(GraphView g, WalkJob J, unsigned long long* __restr
           for (int kk = k; kk < J.l; ++kk) row[kk] = -1;
         break;
       }
-      const int32_t x = warp_binned_step(g, alive, t, v, k, (uint64_t)wid, J.seed, J.a_p, J.a_q, thr, sbuf, cap, lane);
+      const int32_t x = warp_binned_step(g, alive, t, v, k, (uint64_t)wid, J.seed, J.a_p, J.a_q, L.thread_max_deg, sm,
+                                         L.stream_ratio, lane);
       if (mine) row[k] = alive ? x : -1;
       if (alive) {
         if (x < 0) {
@@ -159,14 +161,16 @@ __global__ void k_traffic(const int64_t* __restrict__ rp, int weighted, const in
 // ---------------------------------------------------------------------------
 // launch configuration
 
-static int smem_per_block(int threads, int cap) { return (threads / 32) * cap * (int)sizeof(uint32_t); }
+static int smem_per_block(const LaunchCfg& c) { return (c.block_threads / 32) * warp_smem_bytes(c); }
 
 LaunchCfg resolve_launch(const n2v_graph* g, int variant) {
   LaunchCfg c{};
   c.block_threads = g->tune.block_threads;
   c.thread_max_deg = g->tune.thread_max_deg;
   c.smem_specials = g->tune.smem_specials;
-  const int smem = smem_per_block(c.block_threads, c.smem_specials);
+  c.hash_cap = g->tune.hash_cap;
+  c.stream_ratio = g->tune.stream_ratio;
+  const int smem = smem_per_block(c);
   int per_sm = g->tune.blocks_per_sm;
   if (per_sm <= 0) {
     per_sm = 1;
@@ -218,14 +222,14 @@ static cudaError_t issue(const n2v_graph* g, const WalkCall& c, cudaStream_t s) 
     return cudaGetLastError();
   }
   const LaunchCfg L = resolve_launch(g, base);
-  const int smem = smem_per_block(L.block_threads, L.smem_specials);
+  const int smem = smem_per_block(L);
   if (base == N2V_BINNED) {
     if (smem > 48 * 1024) cudaFuncSetAttribute(k_binned_step, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     const int64_t warps = (c.count + 31) / 32;
     const int wpb = L.block_threads / 32;
     const unsigned blocks = (unsigned)((warps + wpb - 1) / wpb);
     for (int k = 0; k < c.l; ++k)
-      k_binned_step<<<blocks, L.block_threads, smem, s>>>(g->view, J, k, L.thread_max_deg, L.smem_specials);
+      k_binned_step<<<blocks, L.block_threads, smem, s>>>(g->view, J, k, L);
     return cudaGetLastError();
   }
   // persistent
@@ -241,7 +245,7 @@ static cudaError_t issue(const n2v_graph* g, const WalkCall& c, cudaStream_t s) 
     Jc.walk_begin = c.walk_begin + lo;
     Jc.count = std::min<int64_t>(per, c.count - lo);
     Jc.walks = c.walks + lo * (int64_t)c.l;
-    k_persistent<<<L.blocks, L.block_threads, smem, s>>>(g->view, Jc, counters + ci, L.thread_max_deg, L.smem_specials);
+    k_persistent<<<L.blocks, L.block_threads, smem, s>>>(g->view, Jc, counters + ci, L);
   }
   return cudaGetLastError();
 }

@@ -25,8 +25,10 @@ TUNES = {
     "all_warp": dict(thread_max_deg=0),
     "all_thread": dict(thread_max_deg=1 << 30),
     "spill": dict(thread_max_deg=0, smem_specials=32),
-    "hubs": dict(thread_max_deg=0, hub_count=4096, hub_min_degree=2),
+    "hubs": dict(thread_max_deg=0, hub_count=4096, hub_min_degree=2, stream_ratio=0),
     "chunks": dict(chunk_walkers=1000, block_threads=128),
+    "probe": dict(thread_max_deg=0, stream_ratio=0),
+    "pieces": dict(thread_max_deg=0, stream_ratio=100_000, hash_cap=32, smem_specials=32),
 }
 
 
@@ -99,11 +101,16 @@ def test_er_cuda_graph_replay(er):
     g, starts, wl, want = er
     p, q = wl.pq[0]
     graph = n2v.Graph.from_csr(g)
-    for _ in range(2):  # record, then replay
-        got = gpu_rows(g, starts, wl.r, wl.l, p, q, wl.seed, "persistent", cuda_graph=True, graph=graph)
+    # the legacy default stream cannot be recorded
+    with pytest.raises(n2v.N2VError):
+        n2v.walk(graph, starts, wl.r, wl.l, p, q, wl.seed, "persistent", cuda_graph=True, stream=0)
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        for _ in range(2):  # record, then replay
+            got = gpu_rows(g, starts, wl.r, wl.l, p, q, wl.seed, "persistent", cuda_graph=True, graph=graph)
+            np.testing.assert_array_equal(got, want)
+        got = gpu_rows(g, starts, wl.r, wl.l, p, q, wl.seed, "plain", cuda_graph=True, graph=graph)
         np.testing.assert_array_equal(got, want)
-    got = gpu_rows(g, starts, wl.r, wl.l, p, q, wl.seed, "plain", cuda_graph=True, graph=graph)
-    np.testing.assert_array_equal(got, want)
 
 
 def test_er_traffic_matches_oracle(er):
@@ -139,7 +146,7 @@ def test_rmat14_full_output(weighted, pq):
     p, q = pq
     starts = np.arange(g.n, dtype=np.int32)
     want = oracle_rows(g, starts, 20, p, q, 77, np.arange(g.n * 2))
-    for tname in ["default", "hubs", "spill"]:
+    for tname in ["default", "hubs", "spill", "probe", "pieces"]:
         graph = n2v.Graph.from_csr(g, tune=n2v.default_tune(**TUNES[tname]))
         for v in VARIANTS:
             got = gpu_rows(g, starts, 2, 20, p, q, 77, v, graph=graph)
@@ -169,10 +176,12 @@ def test_rmat20_workload(rmat20, pq):
     wl = G.WORKLOADS["rmat20"]
     p, q = pq
     starts = np.arange(g.n, dtype=np.int32)
-    outs = {v: n2v.walk(graph, starts, wl.r, wl.l, p, q, wl.seed, v) for v in VARIANTS}
+    outs = {v: n2v.walk(graph, starts, wl.r, wl.l, p, q, wl.seed, v) for v in ["binned", "persistent"]}
+    # the plain sampler on the first round (every start vertex once)
+    outs["plain"] = n2v.walk(graph, starts, wl.r, wl.l, p, q, wl.seed, "plain", walk_count=g.n)
     assert n2v.n2v_stream_status(graph.handle) == n2v.N2V_OK
-    for v in VARIANTS[:-1]:
-        assert torch.equal(outs[v], outs["persistent"]), v
+    assert torch.equal(outs["binned"], outs["persistent"])
+    assert torch.equal(outs["plain"], outs["persistent"][: g.n])
     ids = sample_ids(g, g.n, wl.r, 3000, 1)
     want = oracle_rows(g, starts, wl.l, p, q, wl.seed, ids)
     got = outs["persistent"][torch.from_numpy(ids).cuda()].cpu().numpy()
@@ -203,7 +212,7 @@ def test_long_lists_star_and_twin_hubs():
     for g in [big_star(1 << 18), two_hubs(3000, extra=50)]:
         starts = np.arange(min(g.n, 4000), dtype=np.int32)
         want = oracle_rows(g, starts, 5, 0.5, 2.0, 3, np.arange(starts.size))
-        for tname in ["default", "hubs", "spill"]:
+        for tname in ["default", "hubs", "spill", "probe", "pieces"]:
             graph = n2v.Graph.from_csr(g, tune=n2v.default_tune(**TUNES[tname]))
             for v in VARIANTS:
                 got = gpu_rows(g, starts, 1, 5, 0.5, 2.0, 3, v, graph=graph)
