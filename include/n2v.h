@@ -88,10 +88,13 @@ typedef struct n2v_tune {
   int32_t hub_min_degree;  /* a vertex needs at least this degree to get a hashed set         */
   int32_t chunk_walkers;   /* walkers per persistent launch (0 = all in one launch)           */
   int32_t hub_budget_mb;   /* MiB of device memory for all hub hash sets (8 bytes per slot)   */
-  int32_t hash_cap;        /* entries of the per-warp shared-memory hash of the shorter list   */
-  int32_t stream_ratio;    /* x10: stream the longer list when its length is at most
+  int32_t stage_window;    /* elements per shared-memory window that stages the longer list of
+                              a step by TMA bulk copies (power of two, 64..4096; 0 = never) */
+  int32_t stream_ratio;    /* x10: stage the longer list when its length is at most
                               stream_ratio/10 * 32*ceil(short/32) * log2(long) (else probe it) */
-  int32_t reserved[6];     /* must be zero                                                    */
+  int32_t spill_specials;  /* per-warp device-workspace slots for special neighbours that do
+                              not fit in shared memory (persistent sampler)                 */
+  int32_t reserved[5];     /* must be zero                                                    */
 } n2v_tune;
 
 /* Fill *t with the library defaults. */
@@ -120,7 +123,8 @@ int n2v_graph_aux_bytes(int64_t n, int64_t nnz, int weighted, const n2v_tune* t,
 
 /* Validate a device-resident CSR graph and build its auxiliary structures in
  * `aux` (device memory of at least n2v_graph_aux_bytes bytes, 256-byte
- * aligned).  row_ptr, col, w and aux are BORROWED device pointers: the
+ * aligned).  col must be 16-byte aligned (it is read by bulk copies) and
+ * every degree must be below 2^30.  row_ptr, col, w and aux are BORROWED device pointers: the
  * caller keeps them alive until n2v_graph_free.  w may be NULL (unweighted).
  * Synchronises `stream` (this is set-up, not the hot path).  Returns
  * N2V_ERR_INVALID_GRAPH for a non-canonical CSR, N2V_ERR_NO_MEM when

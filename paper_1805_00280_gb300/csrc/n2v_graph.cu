@@ -220,10 +220,11 @@ static bool tune_ok(const n2v_tune& t) {
   if (t.block_threads < 64 || t.block_threads > 1024 || t.block_threads % 32) return false;
   if (t.blocks_per_sm < 0 || t.thread_max_deg < 0 || t.smem_specials < 32 || t.smem_specials > 8192) return false;
   if (t.hub_count < 0 || t.hub_min_degree < 0 || t.chunk_walkers < 0 || t.hub_budget_mb < 0) return false;
-  if (t.hash_cap < 32 || t.hash_cap > 4096 || (t.hash_cap & (t.hash_cap - 1)) || t.stream_ratio < 0 ||
-      t.stream_ratio > 1000000)
+  if (t.stage_window != 0 && (t.stage_window < 64 || t.stage_window > 4096 || (t.stage_window & (t.stage_window - 1))))
     return false;
-  for (int i = 0; i < 6; ++i)
+  if (t.stream_ratio < 0 || t.stream_ratio > 1000000 || t.spill_specials < 0 || t.spill_specials > (1 << 24)) return false;
+  if (t.smem_specials % 32) return false;
+  for (int i = 0; i < 5; ++i)
     if (t.reserved[i]) return false;
   return true;
 }
@@ -245,8 +246,9 @@ void n2v_tune_default(n2v_tune* t) {
   t->hub_min_degree = 256;
   t->chunk_walkers = 0;
   t->hub_budget_mb = 1024;
-  t->hash_cap = 512;
+  t->stage_window = 512;
   t->stream_ratio = 40;
+  t->spill_specials = 4096;
 }
 
 int n2v_graph_aux_bytes(int64_t n, int64_t nnz, int weighted, const n2v_tune* t, size_t* bytes) {
@@ -264,7 +266,7 @@ int n2v_graph_load(const int64_t* row_ptr, const int32_t* col, const uint32_t* w
   if (!out) return N2V_ERR_INVALID_ARG;
   *out = nullptr;
   if (!row_ptr || (!col && nnz > 0) || !aux || n < 1 || nnz < 0 || n > INT32_MAX) return N2V_ERR_INVALID_ARG;
-  if (((uintptr_t)aux & 255) != 0) return N2V_ERR_INVALID_ARG;
+  if (((uintptr_t)aux & 255) != 0 || ((uintptr_t)col & 15) != 0) return N2V_ERR_INVALID_ARG;
   n2v_tune tt;
   n2v_tune_default(&tt);
   if (t) tt = *t;
@@ -295,6 +297,7 @@ int n2v_graph_load(const int64_t* row_ptr, const int32_t* col, const uint32_t* w
   g->view.w = w;
   g->view.wpre = weighted ? (const uint64_t*)(a + L.wpre) : nullptr;
   g->view.n = n;
+  g->view.nnz = nnz;
 
   int rc = N2V_OK;
   unsigned long long sc[kScWords];
@@ -306,6 +309,8 @@ int n2v_graph_load(const int64_t* row_ptr, const int32_t* col, const uint32_t* w
       rc = N2V_ERR_CUDA;
   }
   if (rc == N2V_OK && sc[kScBad]) rc = N2V_ERR_INVALID_GRAPH;
+  // the samplers pack a neighbour's index into 30 bits
+  if (rc == N2V_OK && sc[kScMaxDeg] >= (1ull << 30)) rc = N2V_ERR_INVALID_ARG;
   if (rc == N2V_OK) {
     g->info.n = n;
     g->info.nnz = nnz;

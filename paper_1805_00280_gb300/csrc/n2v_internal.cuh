@@ -26,6 +26,7 @@ struct GraphView {
   const uint32_t* __restrict__ w;      // [nnz] or null (unweighted)
   const uint64_t* __restrict__ wpre;   // [nnz] row-local inclusive prefix of w (weighted only)
   int64_t n;
+  int64_t nnz;
   // hashed neighbour sets of hub vertices (FN-Cache analogue); hub_of null = none
   const int32_t* __restrict__ hub_of;    // [n] hub slot or -1
   const int64_t* __restrict__ hub_off;   // [H] first slot of the hub's table
@@ -51,15 +52,58 @@ struct LaunchCfg {
   int block_threads;
   int blocks;
   int thread_max_deg;
-  int smem_specials;  // per warp
-  int hash_cap;       // per warp: entries of the shared-memory hash (2x slots)
-  int stream_ratio;   // x10
+  int smem_specials;   // per warp
+  int stage_window;    // per warp: elements of each of the two staging windows (0 = no staging)
+  int stream_ratio;    // x10
+  int spill_specials;  // per warp, in the device workspace (persistent sampler only)
 };
 
-// Shared memory of one warp: the hash table (2 * hash_cap int2 slots), then
-// the specials buffer (smem_specials uint32), rounded to 16 bytes.
+// Shared memory of one warp: two mbarriers (16 bytes), the specials buffer
+// (smem_specials uint32), then two staging windows of stage_window + 8
+// int32 each (16-byte aligned).
 __host__ __device__ __forceinline__ int warp_smem_bytes(const LaunchCfg& c) {
-  return (2 * c.hash_cap * 8 + c.smem_specials * 4 + 15) & ~15;
+  const int win = c.stage_window > 0 ? 2 * (c.stage_window + 8) * 4 : 0;
+  return 16 + c.smem_specials * 4 + win;
+}
+
+// ---------------------------------------------------------------------------
+// mbarrier and TMA bulk-copy primitives (inline PTX, sm_90+ / sm_103a).
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+// One-dimensional bulk copy global -> shared, completing `bytes` transactions
+// on `bar`.  dst, src and bytes must be multiples of 16.
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for the phase with the given parity to complete, giving up after about
+// two seconds of SM clock (returns false then).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > (1ll << 32)) return false;
+  }
+  return true;
 }
 
 // ---------------------------------------------------------------------------

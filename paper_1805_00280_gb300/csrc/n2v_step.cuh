@@ -73,204 +73,275 @@ __device__ __forceinline__ int32_t thread_step(const GraphView& g, int64_t t, in
 // The specials are N(v) intersected with S = N(t) + {t}.  A generator emits
 // them in increasing position, 32 candidates per call of its callback (one
 // per lane), in one of two ways:
-//   probe  -- walk the shorter list; find each element in the longer one by
-//             binary search (or the hashed set of a hub): about
-//             ceil(short/32) * log2(long) dependent loads;
-//   stream -- put the shorter list in a shared-memory hash table and stream the
-//             longer one with coalesced, prefetched loads: (short + long)/32
-//             independent loads.  A shorter list larger than the table is cut
-//             into value ranges, each streamed against its window of the
-//             longer list.
+//   probe -- walk the shorter list; find each element in the longer one by
+//            binary search in global memory (or the hashed set of a hub):
+//            about ceil(short/32) * log2(long) dependent loads;
+//   stage -- stream the longer list through two shared-memory windows filled
+//            by TMA bulk copies (double-buffered) and binary-search the
+//            shorter list's elements inside the resident window: the bytes
+//            of the longer list move without instructions, and every probe is
+//            a shared-memory access.
 // Both give the same specials, so the choice only changes speed.
 
 struct WarpSmem {
-  uint32_t* spec;  // cap entries: pos | class << 30
+  uint64_t* bar;     // 2 mbarriers (one per staging window)
+  uint32_t* spec;    // cap entries: pos | class << 30
   int cap;
-  int2* htab;      // 2 * hcap slots (key, value); key -1 = empty
-  int hcap;
+  int32_t* win;      // 2 windows of (wlen + 8) int32, 16-byte aligned
+  int wlen;          // elements per window (0 = no staging)
+  uint32_t* spill;   // per-warp device workspace for specials beyond cap (may be null)
+  int spill_cap;
+  uint32_t parity;   // bit b: parity of the next phase of bar[b]
+  bool timed_out;    // a bounded wait gave up
 };
 
-__device__ __forceinline__ WarpSmem warp_smem(unsigned char* base, int warp, const LaunchCfg& L) {
+__device__ __forceinline__ WarpSmem warp_smem(unsigned char* base, int warp, const LaunchCfg& L, uint32_t* spill) {
   WarpSmem w;
-  w.htab = (int2*)(base + (size_t)warp * warp_smem_bytes(L));
-  w.hcap = L.hash_cap;
-  w.spec = (uint32_t*)(w.htab + 2 * L.hash_cap);
+  unsigned char* p = base + (size_t)warp * warp_smem_bytes(L);
+  w.bar = (uint64_t*)p;
+  w.spec = (uint32_t*)(p + 16);
   w.cap = L.smem_specials;
+  w.win = (int32_t*)(p + 16 + L.smem_specials * 4);
+  w.wlen = L.stage_window;
+  w.spill = spill;
+  w.spill_cap = spill ? L.spill_specials : 0;
+  w.parity = 0;
+  w.timed_out = false;
   return w;
+}
+
+// Initialise this warp's mbarriers (once per kernel, whole warp).
+__device__ __forceinline__ void warp_smem_init(WarpSmem& w, int lane) {
+  if (w.wlen > 0 && lane == 0) {
+    mbar_init(&w.bar[0], 1);
+    mbar_init(&w.bar[1], 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
 }
 
 struct StepCtx {
   const GraphView* g;
-  int64_t bv, dv, bt, dt;
+  int64_t bv;
+  int dv, dt;      // degrees (< 2^31: col is indexed by int32 vertex ids)
   const int32_t* __restrict__ nv;
   const int32_t* __restrict__ nt;
   int32_t t32;
-  int64_t ins;     // index of t inside S = N(t) + {t}
+  int ins;         // index of t inside S = N(t) + {t}
   bool has_self;   // t already in N(t) (self-loop at t)
-  int64_t slen;    // |S|
+  int slen;        // |S|
 };
 
 // i-th element of S = N(t) + {t} (sorted, no duplicate)
-__device__ __forceinline__ int32_t s_at(const StepCtx& c, int64_t i) {
+__device__ __forceinline__ int32_t s_at(const StepCtx& c, int i) {
   if (c.has_self || i < c.ins) return __ldg(c.nt + i);
   return i == c.ins ? c.t32 : __ldg(c.nt + i - 1);
 }
-// number of elements of S below val
-__device__ __forceinline__ int64_t s_lower(const StepCtx& c, int32_t val) {
-  int64_t p = lower_bound_i32(c.nt, c.dt, val);
-  if (!c.has_self && c.t32 < val) ++p;
-  return p;
-}
 
-__device__ __forceinline__ uint32_t smem_hash(int32_t x, int bits) { return ((uint32_t)x * 2654435769u) >> (32 - bits); }
+__device__ __forceinline__ int ceil_log2(int x) { return x <= 1 ? 0 : 32 - __clz(x - 1); }
 
-// value stored for key x, or -1; the table is at most half full
-__device__ __forceinline__ int32_t smem_find(const int2* tab, int bits, int32_t x) {
-  const uint32_t mask = (1u << bits) - 1u;
-  uint32_t s = smem_hash(x, bits);
-  for (uint32_t probe = 0; probe <= mask; ++probe) {
-    const int2 e = tab[s];
-    if (e.x == x) return e.y;
-    if (e.x < 0) return -1;
-    s = (s + 1u) & mask;
+// First index i in [0, n) with a[i] >= key (n if none); 32-bit lengths.
+__device__ __forceinline__ int lower_bound32(const int32_t* __restrict__ a, int n, int32_t key) {
+  int lo = 0;
+  while (n > 0) {
+    const int half = n >> 1;
+    if (__ldg(a + lo + half) < key) {
+      lo += half + 1;
+      n -= half + 1;
+    } else {
+      n = half;
+    }
   }
-  return -1;
+  return lo;
 }
 
-__device__ __forceinline__ void smem_insert(int2* tab, int bits, int32_t x, int32_t val) {
-  const uint32_t mask = (1u << bits) - 1u;
-  uint32_t s = smem_hash(x, bits);
-  for (uint32_t probe = 0; probe <= mask; ++probe) {
-    if (atomicCAS(&tab[s].x, -1, x) == -1) {
-      tab[s].y = val;
-      return;
-    }
-    s = (s + 1u) & mask;
+// Fill staging window wi of list L (length llen) into buffer wi & 1: the
+// 16-byte-aligned body by one TMA bulk copy, the ragged tail that would read
+// past the 16-byte-aligned end of col by plain loads.  Returns the element
+// offset of L[wi * wlen] inside the buffer.
+__device__ __forceinline__ int stage_issue(WarpSmem& sm, const GraphView& g, const int32_t* L, int llen, int wi,
+                                           int lane) {
+  const int b = wi & 1;
+  int32_t* buf = sm.win + b * (sm.wlen + 8);
+  const int32_t* src = L + wi * sm.wlen;
+  const int cnt = min(sm.wlen, llen - wi * sm.wlen);
+  const uintptr_t a = (uintptr_t)src, e = (uintptr_t)(src + cnt);
+  const uintptr_t a16 = a & ~(uintptr_t)15;
+  uintptr_t e16 = (e + 15) & ~(uintptr_t)15;
+  const uintptr_t lim = (uintptr_t)(g.col + g.nnz) & ~(uintptr_t)15;  // never read past the end of col
+  if (e16 > lim) e16 = lim;
+  const uint32_t bytes = e16 > a16 ? (uint32_t)(e16 - a16) : 0u;
+  const int off = (int)((a - a16) >> 2);
+  const int tail0 = bytes ? (int)((e16 - a) >> 2) : 0;  // first element not covered by the copy
+  for (int i = tail0 + lane; i < cnt; i += 32) buf[off + i] = __ldg(src + i);
+  __syncwarp();
+  if (lane == 0) {
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(&sm.bar[b], bytes);
+    if (bytes) bulk_copy_g2s(buf, (const void*)a16, bytes, &sm.bar[b]);
   }
+  return off;
 }
 
-__device__ __forceinline__ int ceil_log2(int64_t x) {
-  return x <= 1 ? 0 : 64 - __clzll((unsigned long long)(x - 1));
+__device__ __forceinline__ void stage_wait(WarpSmem& sm, int b) {
+  if (!mbar_wait_bounded(&sm.bar[b], (sm.parity >> b) & 1u)) sm.timed_out = true;
+  sm.parity ^= 1u << b;
+  __syncwarp();
 }
 
-// probe mode, candidates = N(v): class of x_j from a membership test in N(t)
-template <class F>
-__device__ __forceinline__ bool gen_probe_v(const StepCtx& c, int32_t hub_t, F&& f, int lane) {
-  for (int64_t c0 = 0; c0 < c.dv; c0 += 32) {
-    const int64_t i = c0 + lane;
-    int32_t pos = -1;
-    uint32_t cls = 0;
-    if (i < c.dv) {
-      const int32_t x = __ldg(c.nv + i);
-      bool sp;
-      if (x == c.t32) sp = true;
-      else if (hub_t >= 0) sp = hub_find(*c.g, hub_t, x) >= 0;
-      else sp = contains_i32(c.nt, c.dt, x);
-      if (sp) {
-        pos = (int32_t)i;
-        cls = x == c.t32 ? 2u : 1u;
-      }
+// Where the specials of a step go: ordinals [skip, skip + cap + spill_cap)
+// are kept (shared memory first, then the warp's spill area); every special
+// adds its correction (alpha - a_q) * w to the lane's partial sum.
+struct SpecialSink {
+  int cnt;          // specials seen so far (uniform)
+  uint64_t dpart;   // this lane's share of sum (alpha - a_q) * w
+  int skip;
+  int cap;          // shared-memory slots
+  int keep;         // cap + spill slots
+};
+
+__device__ __forceinline__ uint64_t special_delta(const GraphView& g, int64_t bv, int32_t pos, uint32_t cls, uint32_t a_p,
+                                                  uint32_t a_q) {
+  if (!cls) return 0ull;
+  const uint64_t a = cls == 2u ? (uint64_t)a_p : (uint64_t)kAlphaOne;
+  const uint64_t wt = g.w ? (uint64_t)__ldg(g.w + bv + pos) : 1ull;
+  return (a - (uint64_t)a_q) * wt;
+}
+
+__device__ __forceinline__ void sink_emit(SpecialSink& k, WarpSmem& sm, const GraphView& g, int64_t bv, int32_t pos,
+                                          uint32_t cls, uint32_t a_p, uint32_t a_q, int lane) {
+  k.dpart += special_delta(g, bv, pos, cls, a_p, a_q);
+  const unsigned m = __ballot_sync(kFull, cls != 0u);
+  if (cls) {
+    const int ord = k.cnt + __popc(m & lanemask_lt()) - k.skip;
+    if (ord >= 0 && ord < k.keep) {
+      const uint32_t e = (uint32_t)pos | (cls << 30);
+      if (ord < k.cap) sm.spec[ord] = e;
+      else sm.spill[ord - k.cap] = e;
     }
-    if (f(pos, cls)) return true;
   }
-  return false;
+  k.cnt += __popc(m);
 }
 
-// probe mode, candidates = S: position of y in N(v)
-template <class F>
-__device__ __forceinline__ bool gen_probe_t(const StepCtx& c, int32_t hub_v, F&& f, int lane) {
-  for (int64_t c0 = 0; c0 < c.slen; c0 += 32) {
-    const int64_t i = c0 + lane;
-    int32_t pos = -1;
-    uint32_t cls = 0;
-    if (i < c.slen) {
-      const int32_t y = s_at(c, i);
-      int64_t p;
-      if (hub_v >= 0) {
-        p = hub_find(*c.g, hub_v, y);
-      } else {
-        p = lower_bound_i32(c.nv, c.dv, y);
-        if (p >= c.dv || __ldg(c.nv + p) != y) p = -1;
+// Enumerate the specials of the step in increasing position into `k`.
+// mode 0: probe over N(v) (membership in N(t)); 1: probe over S (position in
+// N(v)); 2: stage N(v), candidates S; 3: stage N(t), candidates N(v).
+__device__ __forceinline__ void gen_specials(const StepCtx& c, int mode, int32_t hub, WarpSmem& sm, SpecialSink& k,
+                                             uint32_t a_p, uint32_t a_q, int lane) {
+  const GraphView& g = *c.g;
+  if (mode == 0) {
+    for (int c0 = 0; c0 < c.dv; c0 += 32) {
+      const int i = c0 + lane;
+      int32_t pos = -1;
+      uint32_t cls = 0;
+      if (i < c.dv) {
+        const int32_t x = __ldg(c.nv + i);
+        bool sp;
+        if (x == c.t32) sp = true;
+        else if (hub >= 0) sp = hub_find(g, hub, x) >= 0;
+        else {
+          const int p = lower_bound32(c.nt, c.dt, x);
+          sp = p < c.dt && __ldg(c.nt + p) == x;
+        }
+        if (sp) {
+          pos = i;
+          cls = x == c.t32 ? 2u : 1u;
+        }
       }
-      if (p >= 0) {
-        pos = (int32_t)p;
-        cls = y == c.t32 ? 2u : 1u;
-      }
+      sink_emit(k, sm, g, c.bv, pos, cls, a_p, a_q, lane);
     }
-    if (f(pos, cls)) return true;
+    return;
   }
-  return false;
-}
-
-// stream mode.  hash_s: the table holds S (value = class) and N(v) is
-// streamed; otherwise the table holds N(v) (value = position) and S is
-// streamed.
-template <class F>
-__device__ __forceinline__ bool gen_stream(const StepCtx& c, bool hash_s, const WarpSmem& sm, F&& f, int lane) {
-  constexpr int U = 4;  // chunks of 32 loads in flight
-  const int64_t hlen = hash_s ? c.slen : c.dv;
-  const int64_t llen = hash_s ? c.dv : c.slen;
-  for (int64_t h0 = 0; h0 < hlen; h0 += sm.hcap) {
-    const int64_t h1 = min(h0 + (int64_t)sm.hcap, hlen);
-    const int bits = max(6, ceil_log2(2 * (h1 - h0)));
-    // the window of the streamed list whose values fall in this piece's range
-    int64_t w0 = 0, w1 = llen;
-    if (h0 > 0) {
-      const int32_t lo = hash_s ? s_at(c, h0) : __ldg(c.nv + h0);
-      w0 = hash_s ? lower_bound_i32(c.nv, c.dv, lo) : s_lower(c, lo);
-    }
-    if (h1 < hlen) {
-      const int32_t hi = hash_s ? s_at(c, h1) : __ldg(c.nv + h1);
-      w1 = hash_s ? lower_bound_i32(c.nv, c.dv, hi) : s_lower(c, hi);
-    }
-    __syncwarp();
-    for (int s = lane; s < (1 << bits); s += 32) sm.htab[s] = make_int2(-1, -1);
-    __syncwarp();
-    for (int64_t j = h0 + lane; j < h1; j += 32) {
-      if (hash_s) {
-        const int32_t y = s_at(c, j);
-        smem_insert(sm.htab, bits, y, y == c.t32 ? 2 : 1);
-      } else {
-        smem_insert(sm.htab, bits, __ldg(c.nv + j), (int32_t)j);
+  if (mode == 1) {
+    for (int c0 = 0; c0 < c.slen; c0 += 32) {
+      const int i = c0 + lane;
+      int32_t pos = -1;
+      uint32_t cls = 0;
+      if (i < c.slen) {
+        const int32_t y = s_at(c, i);
+        int p;
+        if (hub >= 0) {
+          p = hub_find(g, hub, y);
+        } else {
+          p = lower_bound32(c.nv, c.dv, y);
+          if (p >= c.dv || __ldg(c.nv + p) != y) p = -1;
+        }
+        if (p >= 0) {
+          pos = p;
+          cls = y == c.t32 ? 2u : 1u;
+        }
       }
+      sink_emit(k, sm, g, c.bv, pos, cls, a_p, a_q, lane);
     }
-    __syncwarp();
-    for (int64_t c0 = w0; c0 < w1; c0 += 32 * U) {
-      int32_t e[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int64_t i = c0 + u * 32 + lane;
-        e[u] = -1;
-        if (i < w1) e[u] = hash_s ? __ldg(c.nv + i) : s_at(c, i);
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        if (c0 + u * 32 >= w1) break;  // uniform
-        const int64_t i = c0 + u * 32 + lane;
-        int32_t pos = -1;
-        uint32_t cls = 0;
-        if (i < w1) {
-          const int32_t val = smem_find(sm.htab, bits, e[u]);
-          if (val >= 0) {
-            if (hash_s) {
-              pos = (int32_t)i;
-              cls = (uint32_t)val;
-            } else {
-              pos = val;
-              cls = e[u] == c.t32 ? 2u : 1u;
-            }
+    return;
+  }
+  // stage: the longer list flows through the two windows; the candidates of
+  // each chunk are searched in the resident window
+  const bool stage_v = mode == 2;
+  const int32_t* L = stage_v ? c.nv : c.nt;
+  const int llen = stage_v ? c.dv : c.dt;
+  const int nkeys = stage_v ? c.slen : c.dv;
+  const int W = sm.wlen;
+  const int nwin = (llen + W - 1) / W;
+  int off0 = stage_issue(sm, g, L, llen, 0, lane);
+  int off1 = nwin > 1 ? stage_issue(sm, g, L, llen, 1, lane) : 0;
+  int wi = 0;
+  stage_wait(sm, 0);
+  for (int kc = 0; kc < nkeys; kc += 32) {
+    const int i = kc + lane;
+    const bool valid = i < nkeys;
+    const int32_t key = valid ? (stage_v ? s_at(c, i) : __ldg(c.nv + i)) : 0;
+    // an element of N(v) equal to t is special whatever N(t) holds
+    const bool is_t = valid && !stage_v && key == c.t32;
+    bool pending = valid && !is_t;
+    int at = -1;  // index of key inside L, or -1
+    for (;;) {
+      const int b = wi & 1;
+      const int32_t* w = sm.win + b * (sm.wlen + 8) + (b ? off1 : off0);
+      const int cnt = min(W, llen - wi * W);
+      const bool last = wi == nwin - 1;
+      if (pending && (last || key <= w[cnt - 1])) {
+        int lo = 0, n = cnt;
+        while (n > 0) {
+          const int half = n >> 1;
+          if (w[lo + half] < key) {
+            lo += half + 1;
+            n -= half + 1;
+          } else {
+            n = half;
           }
         }
-        if (f(pos, cls)) return true;
+        if (lo < cnt && w[lo] == key) at = wi * W + lo;
+        pending = false;
       }
+      if (!__any_sync(kFull, pending)) break;
+      __syncwarp();
+      if (wi + 2 < nwin) {
+        const int o = stage_issue(sm, g, L, llen, wi + 2, lane);
+        if (b) off1 = o; else off0 = o;
+      }
+      ++wi;
+      stage_wait(sm, wi & 1);
     }
+    int32_t pos = -1;
+    uint32_t cls = 0;
+    if (stage_v) {
+      if (at >= 0) {
+        pos = at;
+        cls = key == c.t32 ? 2u : 1u;
+      }
+    } else if (is_t || at >= 0) {
+      pos = i;
+      cls = is_t ? 2u : 1u;
+    }
+    sink_emit(k, sm, g, c.bv, pos, cls, a_p, a_q, lane);
   }
-  return false;
+  // the window after the current one may still be in flight
+  if (wi + 1 < nwin) stage_wait(sm, (wi + 1) & 1);
 }
 
 __device__ __forceinline__ int32_t warp_step(const GraphView& g, int64_t t, int64_t v, int k, uint64_t u,
-                                             uint32_t a_p, uint32_t a_q, const WarpSmem& sm, int stream_ratio,
-                                             int lane) {
+                                             uint32_t a_p, uint32_t a_q, WarpSmem& sm, int stream_ratio, int lane) {
   const int64_t bv = g.rp[v], ev = g.rp[v + 1], dv = ev - bv;
   if (dv == 0) return -1;
   const int32_t* __restrict__ nv = g.col + bv;
@@ -283,122 +354,108 @@ __device__ __forceinline__ int32_t warp_step(const GraphView& g, int64_t t, int6
   StepCtx c;
   c.g = &g;
   c.bv = bv;
-  c.dv = dv;
-  c.bt = g.rp[t];
-  c.dt = g.rp[t + 1] - c.bt;
+  c.dv = (int)dv;
+  const int64_t bt = g.rp[t];
+  c.dt = (int)(g.rp[t + 1] - bt);
   c.nv = nv;
-  c.nt = g.col + c.bt;
+  c.nt = g.col + bt;
   c.t32 = (int32_t)t;
-  c.ins = lower_bound_i32(c.nt, c.dt, c.t32);
+  c.ins = lower_bound32(c.nt, c.dt, c.t32);
   c.has_self = c.ins < c.dt && __ldg(c.nt + c.ins) == c.t32;
   c.slen = c.dt + (c.has_self ? 0 : 1);
   const uint64_t Wv = g.w ? __ldg(g.wpre + ev - 1) : (uint64_t)dv;
 
-  // mode: 0 probe over N(v), 1 probe over S, 2 stream N(v) against a hash of S,
-  // 3 stream S against a hash of N(v)
-  const int64_t shorter = min(dv, c.slen), longer = max(dv, c.slen);
+  const bool v_short = c.dv <= c.slen;
+  const int shorter = v_short ? c.dv : c.slen;
+  const int longer = v_short ? c.dt : c.dv;  // the list that would be staged
+  const int64_t probe_cost = 32ll * ((shorter + 31) / 32) * (ceil_log2(longer + 1) + 1);
   int mode;
   int32_t hub = -1;
-  const bool v_short = dv <= c.slen;
-  const int64_t probe_cost = 32 * ((shorter + 31) / 32) * (int64_t)(ceil_log2(longer + 1) + 1);
-  if (longer * 10 <= (int64_t)stream_ratio * probe_cost) {
+  if (sm.wlen > 0 && longer > 64 && longer * 10 <= (int64_t)stream_ratio * probe_cost) {
     mode = v_short ? 3 : 2;
   } else {
     mode = v_short ? 0 : 1;
     if (g.hub_of) hub = __ldg(g.hub_of + (v_short ? t : v));
   }
-  const int cap_eff = dv < ((int64_t)1 << 30) ? sm.cap : 0;
 
-  auto delta = [&](int32_t pos, uint32_t cls) -> uint64_t {
-    if (!cls) return 0ull;
-    const uint64_t a = cls == 2u ? (uint64_t)a_p : (uint64_t)kAlphaOne;
-    const uint64_t wt = g.w ? (uint64_t)__ldg(g.w + bv + pos) : 1ull;
-    return (a - (uint64_t)a_q) * wt;
-  };
-  auto Wat = [&](int64_t pos) -> uint64_t {
-    return pos < 0 ? 0ull : (g.w ? __ldg(g.wpre + bv + pos) : (uint64_t)(pos + 1));
-  };
-  auto generate = [&](auto&& f) -> bool {
-    switch (mode) {
-      case 0: return gen_probe_v(c, hub, f, lane);
-      case 1: return gen_probe_t(c, hub, f, lane);
-      case 2: return gen_stream(c, true, sm, f, lane);
-      default: return gen_stream(c, false, sm, f, lane);
-    }
-  };
+  SpecialSink sk;
+  sk.cnt = 0;
+  sk.dpart = 0;
+  sk.skip = 0;
+  sk.cap = sm.cap;  // positions are packed in 30 bits: degrees < 2^30 (checked at load)
+  sk.keep = sk.cap + sm.spill_cap;
 
-  // pass 1: total, keeping the specials in shared memory while they fit
-  uint64_t part = 0;
-  int64_t cnt = 0;
-  generate([&](int32_t pos, uint32_t cls) -> bool {
-    part += delta(pos, cls);
-    const unsigned m = __ballot_sync(kFull, cls != 0u);
-    const int64_t slot = cnt + __popc(m & lanemask_lt());
-    if (cls && slot < cap_eff) sm.spec[slot] = (uint32_t)pos | (cls << 30);
-    cnt += __popc(m);
-    return false;
-  });
-  const uint64_t T = (uint64_t)a_q * Wv + warp_sum_u64(part);
-  if (T == 0) return -1;
-  const uint64_t r = scale_draw(u, T);
-  __syncwarp();
-
-  // first j in (lo_excl, hi] with a_q * W_j + base > r
-  auto solve_gap = [&](int64_t lo_excl, int64_t hi, uint64_t base) -> int64_t {
-    const uint64_t m = (r - base) / (uint64_t)a_q;
-    if (!g.w) {
-      int64_t j = (int64_t)m;
-      if (j <= lo_excl) j = lo_excl + 1;
-      if (j > hi) j = hi;
-      return j;
+  uint64_t r = 0, D = 0;
+  int prev = -1, chosen = -1;
+  bool found = false;
+  // Pass 1 enumerates every special (and sums the corrections into T); pass 2
+  // walks the kept specials in position order.  If the answer lies beyond
+  // the kept ones, the specials are enumerated again, keeping the next
+  // segment, and the walk continues from where it stopped.
+  for (int seg = 0;; seg += sk.keep) {
+    sk.cnt = 0;
+    sk.skip = seg;
+    gen_specials(c, mode, hub, sm, sk, a_p, a_q, lane);
+    if (seg == 0) {
+      const uint64_t T = (uint64_t)a_q * Wv + warp_sum_u64(sk.dpart);
+      if (T == 0) return -1;
+      r = scale_draw(u, T);
     }
-    return warp_first_above_u64(g.wpre + bv, lo_excl + 1, hi, m, lane);
-  };
-
-  // pass 2: walk the specials in position order, carrying the running D
-  uint64_t D = 0;
-  int64_t prev = -1, chosen = -1;
-  auto search = [&](int32_t pos, uint32_t cls) -> bool {
-    const uint64_t dl = delta(pos, cls);
-    const uint64_t incl = warp_incl_scan_u64(dl, lane) + D;
-    const uint64_t excl = incl - dl;
-    const bool hit = cls != 0u && ((uint64_t)a_q * Wat(pos) + incl > r);
-    const unsigned hm = __ballot_sync(kFull, hit);
-    const unsigned smask = __ballot_sync(kFull, cls != 0u);
-    if (hm) {
-      const int f = __ffs(hm) - 1;
-      const int64_t fpos = __shfl_sync(kFull, (int64_t)pos, f);
-      const uint64_t fexcl = __shfl_sync(kFull, excl, f);
-      const unsigned below = smask & ((1u << f) - 1u);
-      const int64_t pp = __shfl_sync(kFull, (int64_t)pos, below ? 31 - __clz(below) : 0);
-      const int64_t gap_lo = below ? pp : prev;
-      const uint64_t before = (uint64_t)a_q * Wat(fpos - 1) + fexcl;
-      chosen = before > r ? solve_gap(gap_lo, fpos - 1, fexcl) : fpos;
-      return true;
-    }
-    if (smask) {
-      D = __shfl_sync(kFull, incl, 31);
-      prev = __shfl_sync(kFull, (int64_t)pos, 31 - __clz(smask));
-    }
-    return false;
-  };
-  bool found;
-  if (cnt <= cap_eff) {
-    found = false;
-    for (int64_t c0 = 0; c0 < cnt && !found; c0 += 32) {
+    __syncwarp();
+    __threadfence_block();  // spilled specials are read back by other lanes
+    const int n_in = min(sk.cnt - seg, sk.keep);
+    for (int c0 = 0; c0 < n_in; c0 += 32) {
       int32_t pos = -1;
       uint32_t cls = 0;
-      if (c0 + lane < cnt) {
-        const uint32_t e = sm.spec[c0 + lane];
+      const int i = c0 + lane;
+      if (i < n_in) {
+        const uint32_t e = i < sk.cap ? sm.spec[i] : sm.spill[i - sk.cap];
         pos = (int32_t)(e & 0x3fffffffu);
         cls = e >> 30;
       }
-      found = search(pos, cls);
+      const uint64_t dl = special_delta(g, bv, pos, cls, a_p, a_q);
+      const uint64_t incl = warp_incl_scan_u64(dl, lane) + D;
+      const uint64_t excl = incl - dl;
+      const uint64_t Wp = pos < 0 ? 0ull : (g.w ? __ldg(g.wpre + bv + pos) : (uint64_t)(pos + 1));
+      const bool hit = cls != 0u && ((uint64_t)a_q * Wp + incl > r);
+      const unsigned hm = __ballot_sync(kFull, hit);
+      const unsigned smask = __ballot_sync(kFull, cls != 0u);
+      if (hm) {
+        const int f = __ffs(hm) - 1;
+        const int fpos = __shfl_sync(kFull, pos, f);
+        const uint64_t fexcl = __shfl_sync(kFull, excl, f);
+        const unsigned below = smask & ((1u << f) - 1u);
+        const int pp = __shfl_sync(kFull, pos, below ? 31 - __clz(below) : 0);
+        const int gap_lo = below ? pp : prev;
+        const uint64_t Wb = fpos - 1 < 0 ? 0ull : (g.w ? __ldg(g.wpre + bv + fpos - 1) : (uint64_t)fpos);
+        if ((uint64_t)a_q * Wb + fexcl > r) {
+          prev = gap_lo;
+          D = fexcl;
+          chosen = fpos - 1;  // the answer lies in (gap_lo, fpos - 1]
+        } else {
+          chosen = fpos;
+          found = true;
+        }
+        break;
+      }
+      if (smask) {
+        D = __shfl_sync(kFull, incl, 31);
+        prev = __shfl_sync(kFull, pos, 31 - __clz(smask));
+      }
     }
-  } else {
-    found = generate(search);
+    if (found || chosen >= 0 || seg + sk.keep >= sk.cnt) break;
   }
-  if (!found) chosen = solve_gap(prev, dv - 1, D);
+  if (!found) {
+    // first j in (prev, hi] with a_q * W_j + D > r
+    const int hi = chosen >= 0 ? chosen : c.dv - 1;
+    const uint64_t m = (r - D) / (uint64_t)a_q;
+    if (!g.w) {
+      chosen = m > (uint64_t)hi ? hi : (int)m;
+      if (chosen <= prev) chosen = prev + 1;
+    } else {
+      chosen = (int)warp_first_above_u64(g.wpre + bv, prev + 1, hi, m, lane);
+    }
+  }
   __syncwarp();
   return __ldg(nv + chosen);
 }
@@ -409,7 +466,7 @@ __device__ __forceinline__ int32_t warp_step(const GraphView& g, int64_t t, int6
 // taken one after another by the whole warp (warp bin).
 __device__ __forceinline__ int32_t warp_binned_step(const GraphView& g, bool alive, int64_t t, int64_t v, int k,
                                                     uint64_t wid, uint64_t seed, uint32_t a_p, uint32_t a_q,
-                                                    int thr, const WarpSmem& sm, int stream_ratio, int lane) {
+                                                    int thr, WarpSmem& sm, int stream_ratio, int lane) {
   int32_t x = -1;
   bool small = false;
   uint64_t u = 0;

@@ -45,12 +45,13 @@ __global__ void __launch_bounds__(256) k_plain_step(GraphView g, WalkJob J, int 
 // ---------------------------------------------------------------------------
 // Binned: one launch per step k; warp w owns walkers [32w, 32w + 32) and bins
 // each of their steps by degree (own lane, or the whole warp).
-__global__ void k_binned_step(GraphView g, WalkJob J, int k, LaunchCfg L) {
+__global__ void __launch_bounds__(256) k_binned_step(GraphView g, WalkJob J, int k, LaunchCfg L) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const WarpSmem sm = warp_smem(smem_raw, warp, L);
   const int64_t base = ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * 32;
   if (base >= J.count) return;  // uniform per warp
+  WarpSmem sm = warp_smem(smem_raw, warp, L, nullptr);
+  warp_smem_init(sm, lane);
   const int64_t i = base + lane;
   const bool mine = i < J.count;
   const int64_t wid = J.walk_begin + i;
@@ -75,6 +76,7 @@ __global__ void k_binned_step(GraphView g, WalkJob J, int k, LaunchCfg L) {
   const int32_t x = warp_binned_step(g, alive, t, v, k, (uint64_t)wid, J.seed, J.a_p, J.a_q, L.thread_max_deg, sm,
                                      L.stream_ratio, lane);
   if (mine) row[k] = alive ? x : -1;
+  if (sm.timed_out && lane == 0) atomicOr(J.status, kStTimeout);
 }
 
 // ---------------------------------------------------------------------------
@@ -82,11 +84,14 @@ __global__ void k_binned_step(GraphView g, WalkJob J, int k, LaunchCfg L) {
 // time from a device counter and runs them to the end; every step is binned
 // by degree as above.  Walkers are independent (FN-Multi's observation,
 // Section 3.4), so the order in which warps take them does not change any row.
-__global__ void k_persistent(GraphView g, WalkJob J, unsigned long long* __restrict__ counter, LaunchCfg L) {
+__global__ void __launch_bounds__(256, 3) k_persistent(GraphView g, WalkJob J, unsigned long long* __restrict__ counter, LaunchCfg L,
+                             uint32_t* __restrict__ spill) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const WarpSmem sm = warp_smem(smem_raw, warp, L);
-  for (;;) {
+  const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+  WarpSmem sm = warp_smem(smem_raw, warp, L, spill ? spill + gw * (int64_t)L.spill_specials : nullptr);
+  warp_smem_init(sm, lane);
+  while (!sm.timed_out) {
     unsigned long long base = 0;
     if (lane == 0) base = atomicAdd(counter, 32ull);
     base = __shfl_sync(kFull, base, 0);
@@ -107,6 +112,7 @@ __global__ void k_persistent(GraphView g, WalkJob J, unsigned long long* __restr
       }
     }
     for (int k = 0; k < J.l; ++k) {
+      if (sm.timed_out) break;
       if (!__any_sync(kFull, alive)) {
         if (mine)
           for (int kk = k; kk < J.l; ++kk) row[kk] = -1;
@@ -125,6 +131,7 @@ __global__ void k_persistent(GraphView g, WalkJob J, unsigned long long* __restr
       }
     }
   }
+  if (sm.timed_out && lane == 0) atomicOr(J.status, kStTimeout);
 }
 
 // ---------------------------------------------------------------------------
@@ -168,8 +175,9 @@ LaunchCfg resolve_launch(const n2v_graph* g, int variant) {
   c.block_threads = g->tune.block_threads;
   c.thread_max_deg = g->tune.thread_max_deg;
   c.smem_specials = g->tune.smem_specials;
-  c.hash_cap = g->tune.hash_cap;
+  c.stage_window = g->tune.stage_window;
   c.stream_ratio = g->tune.stream_ratio;
+  c.spill_specials = g->tune.spill_specials;
   const int smem = smem_per_block(c);
   int per_sm = g->tune.blocks_per_sm;
   if (per_sm <= 0) {
@@ -189,6 +197,8 @@ static int64_t n_chunks(const n2v_graph* g, int64_t count) {
   if (cw <= 0 || count <= 0) return 1;
   return (count + cw - 1) / cw;
 }
+
+static size_t counter_bytes(int64_t chunks) { return (sizeof(unsigned long long) * (size_t)chunks + 255) & ~(size_t)255; }
 
 struct WalkCall {
   const int32_t* starts;
@@ -239,13 +249,14 @@ static cudaError_t issue(const n2v_graph* g, const WalkCall& c, cudaStream_t s) 
   cudaError_t e = cudaMemsetAsync(counters, 0, sizeof(unsigned long long) * (size_t)chunks, s);
   if (e != cudaSuccess) return e;
   const int64_t per = chunks == 1 ? c.count : g->tune.chunk_walkers;
+  uint32_t* spill = L.spill_specials > 0 ? (uint32_t*)((char*)c.ws + counter_bytes(chunks)) : nullptr;
   for (int64_t ci = 0; ci < chunks; ++ci) {
     WalkJob Jc = J;
     const int64_t lo = ci * per;
     Jc.walk_begin = c.walk_begin + lo;
     Jc.count = std::min<int64_t>(per, c.count - lo);
     Jc.walks = c.walks + lo * (int64_t)c.l;
-    k_persistent<<<L.blocks, L.block_threads, smem, s>>>(g->view, Jc, counters + ci, L);
+    k_persistent<<<L.blocks, L.block_threads, smem, s>>>(g->view, Jc, counters + ci, L, spill);
   }
   return cudaGetLastError();
 }
@@ -323,7 +334,11 @@ int n2v_walk_ws_bytes(const n2v_graph* g, int64_t walk_count, int32_t l, int var
   const int base = variant & 0xff;
   if (base != N2V_PLAIN && base != N2V_BINNED && base != N2V_PERSISTENT) return N2V_ERR_INVALID_ARG;
   size_t b = 0;
-  if (base == N2V_PERSISTENT) b = ((sizeof(unsigned long long) * (size_t)n_chunks(g, walk_count)) + 255) & ~(size_t)255;
+  if (base == N2V_PERSISTENT) {
+    const LaunchCfg L = resolve_launch(g, base);
+    b = counter_bytes(n_chunks(g, walk_count));
+    b += sizeof(uint32_t) * (size_t)L.blocks * (size_t)(L.block_threads / 32) * (size_t)L.spill_specials;
+  }
   *bytes = b;
   return N2V_OK;
 }

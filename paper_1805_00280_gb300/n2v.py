@@ -46,8 +46,8 @@ class n2v_tune(ctypes.Structure):
                 ("thread_max_deg", ctypes.c_int32), ("smem_specials", ctypes.c_int32),
                 ("hub_count", ctypes.c_int32), ("hub_min_degree", ctypes.c_int32),
                 ("chunk_walkers", ctypes.c_int32), ("hub_budget_mb", ctypes.c_int32),
-                ("hash_cap", ctypes.c_int32), ("stream_ratio", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("stage_window", ctypes.c_int32), ("stream_ratio", ctypes.c_int32),
+                ("spill_specials", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
