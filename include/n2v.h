@@ -94,7 +94,8 @@ typedef struct n2v_tune {
                               stream_ratio/10 * 32*ceil(short/32) * log2(long) (else probe it) */
   int32_t spill_specials;  /* per-warp device-workspace slots for special neighbours that do
                               not fit in shared memory (persistent sampler)                 */
-  int32_t reserved[5];     /* must be zero                                                    */
+  int32_t stage_buffers;   /* staging windows in flight per warp (2 or 4)                    */
+  int32_t reserved[4];     /* must be zero                                                    */
 } n2v_tune;
 
 /* Fill *t with the library defaults. */

@@ -224,7 +224,8 @@ static bool tune_ok(const n2v_tune& t) {
     return false;
   if (t.stream_ratio < 0 || t.stream_ratio > 1000000 || t.spill_specials < 0 || t.spill_specials > (1 << 24)) return false;
   if (t.smem_specials % 32) return false;
-  for (int i = 0; i < 5; ++i)
+  if (t.stage_buffers != 2 && t.stage_buffers != 4) return false;
+  for (int i = 0; i < 4; ++i)
     if (t.reserved[i]) return false;
   return true;
 }
@@ -249,6 +250,7 @@ void n2v_tune_default(n2v_tune* t) {
   t->stage_window = 512;
   t->stream_ratio = 40;
   t->spill_specials = 4096;
+  t->stage_buffers = 2;
 }
 
 int n2v_graph_aux_bytes(int64_t n, int64_t nnz, int weighted, const n2v_tune* t, size_t* bytes) {

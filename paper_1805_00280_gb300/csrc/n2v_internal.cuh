@@ -56,14 +56,15 @@ struct LaunchCfg {
   int stage_window;    // per warp: elements of each of the two staging windows (0 = no staging)
   int stream_ratio;    // x10
   int spill_specials;  // per warp, in the device workspace (persistent sampler only)
+  int stage_buffers;   // staging windows per warp (2 or 4)
 };
 
-// Shared memory of one warp: two mbarriers (16 bytes), the specials buffer
-// (smem_specials uint32), then two staging windows of stage_window + 8
-// int32 each (16-byte aligned).
+// Shared memory of one warp: four mbarrier slots (32 bytes), the specials
+// buffer (smem_specials uint32), then stage_buffers staging windows of
+// stage_window + 8 int32 each (16-byte aligned).
 __host__ __device__ __forceinline__ int warp_smem_bytes(const LaunchCfg& c) {
-  const int win = c.stage_window > 0 ? 2 * (c.stage_window + 8) * 4 : 0;
-  return 16 + c.smem_specials * 4 + win;
+  const int win = c.stage_window > 0 ? c.stage_buffers * (c.stage_window + 8) * 4 : 0;
+  return 32 + c.smem_specials * 4 + win;
 }
 
 // ---------------------------------------------------------------------------

@@ -84,11 +84,12 @@ __device__ __forceinline__ int32_t thread_step(const GraphView& g, int64_t t, in
 // Both give the same specials, so the choice only changes speed.
 
 struct WarpSmem {
-  uint64_t* bar;     // 2 mbarriers (one per staging window)
+  uint64_t* bar;     // one mbarrier per staging window
   uint32_t* spec;    // cap entries: pos | class << 30
   int cap;
-  int32_t* win;      // 2 windows of (wlen + 8) int32, 16-byte aligned
+  int32_t* win;      // nbuf windows of (wlen + 8) int32, 16-byte aligned
   int wlen;          // elements per window (0 = no staging)
+  int nbuf;          // windows in flight (2 or 4)
   uint32_t* spill;   // per-warp device workspace for specials beyond cap (may be null)
   int spill_cap;
   uint32_t parity;   // bit b: parity of the next phase of bar[b]
@@ -99,10 +100,11 @@ __device__ __forceinline__ WarpSmem warp_smem(unsigned char* base, int warp, con
   WarpSmem w;
   unsigned char* p = base + (size_t)warp * warp_smem_bytes(L);
   w.bar = (uint64_t*)p;
-  w.spec = (uint32_t*)(p + 16);
+  w.spec = (uint32_t*)(p + 32);
   w.cap = L.smem_specials;
-  w.win = (int32_t*)(p + 16 + L.smem_specials * 4);
+  w.win = (int32_t*)(p + 32 + L.smem_specials * 4);
   w.wlen = L.stage_window;
+  w.nbuf = L.stage_buffers;
   w.spill = spill;
   w.spill_cap = spill ? L.spill_specials : 0;
   w.parity = 0;
@@ -113,8 +115,7 @@ __device__ __forceinline__ WarpSmem warp_smem(unsigned char* base, int warp, con
 // Initialise this warp's mbarriers (once per kernel, whole warp).
 __device__ __forceinline__ void warp_smem_init(WarpSmem& w, int lane) {
   if (w.wlen > 0 && lane == 0) {
-    mbar_init(&w.bar[0], 1);
-    mbar_init(&w.bar[1], 1);
+    for (int b = 0; b < w.nbuf; ++b) mbar_init(&w.bar[b], 1);
     fence_mbar_init();
   }
   __syncwarp();
@@ -155,13 +156,18 @@ __device__ __forceinline__ int lower_bound32(const int32_t* __restrict__ a, int 
   return lo;
 }
 
-// Fill staging window wi of list L (length llen) into buffer wi & 1: the
+// Element offset of L[wi * wlen] inside its staging buffer (the copy starts at
+// the 16-byte boundary below it).
+__device__ __forceinline__ int stage_off(const WarpSmem& sm, const int32_t* L, int wi) {
+  return (int)(((uintptr_t)(L + wi * sm.wlen) & 15) >> 2);
+}
+
+// Fill staging window wi of list L (length llen) into buffer wi % nbuf: the
 // 16-byte-aligned body by one TMA bulk copy, the ragged tail that would read
-// past the 16-byte-aligned end of col by plain loads.  Returns the element
-// offset of L[wi * wlen] inside the buffer.
-__device__ __forceinline__ int stage_issue(WarpSmem& sm, const GraphView& g, const int32_t* L, int llen, int wi,
-                                           int lane) {
-  const int b = wi & 1;
+// past the 16-byte-aligned end of col by plain loads.
+__device__ __forceinline__ void stage_issue(WarpSmem& sm, const GraphView& g, const int32_t* L, int llen, int wi,
+                                            int lane) {
+  const int b = wi & (sm.nbuf - 1);
   int32_t* buf = sm.win + b * (sm.wlen + 8);
   const int32_t* src = L + wi * sm.wlen;
   const int cnt = min(sm.wlen, llen - wi * sm.wlen);
@@ -180,7 +186,6 @@ __device__ __forceinline__ int stage_issue(WarpSmem& sm, const GraphView& g, con
     mbar_arrive_expect_tx(&sm.bar[b], bytes);
     if (bytes) bulk_copy_g2s(buf, (const void*)a16, bytes, &sm.bar[b]);
   }
-  return off;
 }
 
 __device__ __forceinline__ void stage_wait(WarpSmem& sm, int b) {
@@ -283,8 +288,8 @@ __device__ __forceinline__ void gen_specials(const StepCtx& c, int mode, int32_t
   const int nkeys = stage_v ? c.slen : c.dv;
   const int W = sm.wlen;
   const int nwin = (llen + W - 1) / W;
-  int off0 = stage_issue(sm, g, L, llen, 0, lane);
-  int off1 = nwin > 1 ? stage_issue(sm, g, L, llen, 1, lane) : 0;
+  const int ahead = min(sm.nbuf, nwin);
+  for (int q = 0; q < ahead; ++q) stage_issue(sm, g, L, llen, q, lane);
   int wi = 0;
   stage_wait(sm, 0);
   for (int kc = 0; kc < nkeys; kc += 32) {
@@ -296,8 +301,8 @@ __device__ __forceinline__ void gen_specials(const StepCtx& c, int mode, int32_t
     bool pending = valid && !is_t;
     int at = -1;  // index of key inside L, or -1
     for (;;) {
-      const int b = wi & 1;
-      const int32_t* w = sm.win + b * (sm.wlen + 8) + (b ? off1 : off0);
+      const int b = wi & (sm.nbuf - 1);
+      const int32_t* w = sm.win + b * (sm.wlen + 8) + stage_off(sm, L, wi);
       const int cnt = min(W, llen - wi * W);
       const bool last = wi == nwin - 1;
       if (pending && (last || key <= w[cnt - 1])) {
@@ -316,12 +321,9 @@ __device__ __forceinline__ void gen_specials(const StepCtx& c, int mode, int32_t
       }
       if (!__any_sync(kFull, pending)) break;
       __syncwarp();
-      if (wi + 2 < nwin) {
-        const int o = stage_issue(sm, g, L, llen, wi + 2, lane);
-        if (b) off1 = o; else off0 = o;
-      }
+      if (wi + sm.nbuf < nwin) stage_issue(sm, g, L, llen, wi + sm.nbuf, lane);
       ++wi;
-      stage_wait(sm, wi & 1);
+      stage_wait(sm, wi & (sm.nbuf - 1));
     }
     int32_t pos = -1;
     uint32_t cls = 0;
@@ -336,8 +338,8 @@ __device__ __forceinline__ void gen_specials(const StepCtx& c, int mode, int32_t
     }
     sink_emit(k, sm, g, c.bv, pos, cls, a_p, a_q, lane);
   }
-  // the window after the current one may still be in flight
-  if (wi + 1 < nwin) stage_wait(sm, (wi + 1) & 1);
+  // the windows after the current one may still be in flight
+  for (int q = wi + 1; q < nwin && q <= wi + sm.nbuf - 1; ++q) stage_wait(sm, q & (sm.nbuf - 1));
 }
 
 __device__ __forceinline__ int32_t warp_step(const GraphView& g, int64_t t, int64_t v, int k, uint64_t u,
@@ -360,9 +362,9 @@ __device__ __forceinline__ int32_t warp_step(const GraphView& g, int64_t t, int6
   c.nv = nv;
   c.nt = g.col + bt;
   c.t32 = (int32_t)t;
-  c.ins = lower_bound32(c.nt, c.dt, c.t32);
-  c.has_self = c.ins < c.dt && __ldg(c.nt + c.ins) == c.t32;
-  c.slen = c.dt + (c.has_self ? 0 : 1);
+  c.ins = 0;
+  c.has_self = false;
+  c.slen = c.dt + 1;  // |S| unless t has a self-loop; fixed below where S is walked
   const uint64_t Wv = g.w ? __ldg(g.wpre + ev - 1) : (uint64_t)dv;
 
   const bool v_short = c.dv <= c.slen;
@@ -376,6 +378,11 @@ __device__ __forceinline__ int32_t warp_step(const GraphView& g, int64_t t, int6
   } else {
     mode = v_short ? 0 : 1;
     if (g.hub_of) hub = __ldg(g.hub_of + (v_short ? t : v));
+  }
+  if (mode == 1 || mode == 2) {  // these walk S = N(t) + {t} in order
+    c.ins = lower_bound32(c.nt, c.dt, c.t32);
+    c.has_self = c.ins < c.dt && __ldg(c.nt + c.ins) == c.t32;
+    c.slen = c.dt + (c.has_self ? 0 : 1);
   }
 
   SpecialSink sk;

@@ -178,6 +178,7 @@ LaunchCfg resolve_launch(const n2v_graph* g, int variant) {
   c.stage_window = g->tune.stage_window;
   c.stream_ratio = g->tune.stream_ratio;
   c.spill_specials = g->tune.spill_specials;
+  c.stage_buffers = g->tune.stage_buffers;
   const int smem = smem_per_block(c);
   int per_sm = g->tune.blocks_per_sm;
   if (per_sm <= 0) {

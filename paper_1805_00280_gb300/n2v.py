@@ -47,7 +47,8 @@ class n2v_tune(ctypes.Structure):
                 ("hub_count", ctypes.c_int32), ("hub_min_degree", ctypes.c_int32),
                 ("chunk_walkers", ctypes.c_int32), ("hub_budget_mb", ctypes.c_int32),
                 ("stage_window", ctypes.c_int32), ("stream_ratio", ctypes.c_int32),
-                ("spill_specials", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("spill_specials", ctypes.c_int32), ("stage_buffers", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}

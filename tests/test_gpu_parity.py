@@ -30,6 +30,7 @@ TUNES = {
     "probe": dict(thread_max_deg=0, stream_ratio=0),
     # every list longer than 64 staged through many 64-element TMA windows
     "stage": dict(thread_max_deg=0, stream_ratio=100_000, stage_window=64),
+    "stage4": dict(thread_max_deg=0, stream_ratio=100_000, stage_window=64, stage_buffers=4),
     # specials kept 32 at a time: the enumeration restarts segment by segment
     "segments": dict(thread_max_deg=0, smem_specials=32, spill_specials=0, stage_window=64, stream_ratio=100_000),
 }
@@ -149,7 +150,7 @@ def test_rmat14_full_output(weighted, pq):
     p, q = pq
     starts = np.arange(g.n, dtype=np.int32)
     want = oracle_rows(g, starts, 20, p, q, 77, np.arange(g.n * 2))
-    for tname in ["default", "hubs", "spill", "probe", "stage", "segments"]:
+    for tname in ["default", "hubs", "spill", "probe", "stage", "stage4", "segments"]:
         graph = n2v.Graph.from_csr(g, tune=n2v.default_tune(**TUNES[tname]))
         for v in VARIANTS:
             got = gpu_rows(g, starts, 2, 20, p, q, 77, v, graph=graph)
@@ -215,7 +216,7 @@ def test_long_lists_star_and_twin_hubs():
     for g in [big_star(1 << 18), two_hubs(3000, extra=50)]:
         starts = np.arange(min(g.n, 4000), dtype=np.int32)
         want = oracle_rows(g, starts, 5, 0.5, 2.0, 3, np.arange(starts.size))
-        for tname in ["default", "hubs", "spill", "probe", "stage", "segments"]:
+        for tname in ["default", "hubs", "spill", "probe", "stage", "stage4", "segments"]:
             graph = n2v.Graph.from_csr(g, tune=n2v.default_tune(**TUNES[tname]))
             for v in VARIANTS:
                 got = gpu_rows(g, starts, 1, 5, 0.5, 2.0, 3, v, graph=graph)
