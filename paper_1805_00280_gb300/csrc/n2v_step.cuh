@@ -199,6 +199,7 @@ __device__ __forceinline__ void stage_wait(WarpSmem& sm, int b) {
 // adds its correction (alpha - a_q) * w to the lane's partial sum.
 struct SpecialSink {
   int cnt;          // specials seen so far (uniform)
+  int ord_t;        // ordinal of the special x == t (class 2), or -1
   uint64_t dpart;   // this lane's share of sum (alpha - a_q) * w
   int skip;
   int cap;          // shared-memory slots
@@ -217,6 +218,8 @@ __device__ __forceinline__ void sink_emit(SpecialSink& k, WarpSmem& sm, const Gr
                                           uint32_t cls, uint32_t a_p, uint32_t a_q, int lane) {
   k.dpart += special_delta(g, bv, pos, cls, a_p, a_q);
   const unsigned m = __ballot_sync(kFull, cls != 0u);
+  const unsigned m2 = __ballot_sync(kFull, cls == 2u);
+  if (m2) k.ord_t = k.cnt + __popc(m & ((1u << (__ffs(m2) - 1)) - 1u));
   if (cls) {
     const int ord = k.cnt + __popc(m & lanemask_lt()) - k.skip;
     if (ord >= 0 && ord < k.keep) {
@@ -235,12 +238,14 @@ __device__ __forceinline__ void gen_specials(const StepCtx& c, int mode, int32_t
                                              uint32_t a_p, uint32_t a_q, int lane) {
   const GraphView& g = *c.g;
   if (mode == 0) {
+    int32_t x_next = lane < c.dv ? __ldg(c.nv + lane) : 0;
     for (int c0 = 0; c0 < c.dv; c0 += 32) {
       const int i = c0 + lane;
       int32_t pos = -1;
       uint32_t cls = 0;
+      const int32_t x = x_next;
+      if (i + 32 < c.dv) x_next = __ldg(c.nv + i + 32);
       if (i < c.dv) {
-        const int32_t x = __ldg(c.nv + i);
         bool sp;
         if (x == c.t32) sp = true;
         else if (hub >= 0) sp = hub_find(g, hub, x) >= 0;
@@ -291,11 +296,13 @@ __device__ __forceinline__ void gen_specials(const StepCtx& c, int mode, int32_t
   const int ahead = min(sm.nbuf, nwin);
   for (int q = 0; q < ahead; ++q) stage_issue(sm, g, L, llen, q, lane);
   int wi = 0;
+  int32_t key_next = lane < nkeys ? (stage_v ? s_at(c, lane) : __ldg(c.nv + lane)) : 0;
   stage_wait(sm, 0);
   for (int kc = 0; kc < nkeys; kc += 32) {
     const int i = kc + lane;
     const bool valid = i < nkeys;
-    const int32_t key = valid ? (stage_v ? s_at(c, i) : __ldg(c.nv + i)) : 0;
+    const int32_t key = key_next;
+    if (i + 32 < nkeys) key_next = stage_v ? s_at(c, i + 32) : __ldg(c.nv + i + 32);  // next chunk, in flight
     // an element of N(v) equal to t is special whatever N(t) holds
     const bool is_t = valid && !stage_v && key == c.t32;
     bool pending = valid && !is_t;
@@ -306,16 +313,13 @@ __device__ __forceinline__ void gen_specials(const StepCtx& c, int mode, int32_t
       const int cnt = min(W, llen - wi * W);
       const bool last = wi == nwin - 1;
       if (pending && (last || key <= w[cnt - 1])) {
-        int lo = 0, n = cnt;
-        while (n > 0) {
-          const int half = n >> 1;
-          if (w[lo + half] < key) {
-            lo += half + 1;
-            n -= half + 1;
-          } else {
-            n = half;
-          }
+        // fixed-depth search over the power-of-two window (slots >= cnt read as +inf)
+        int lo = 0;
+        for (int s = W >> 1; s > 0; s >>= 1) {
+          const int probe = lo + s - 1;
+          lo += (probe < cnt && w[probe] < key) ? s : 0;
         }
+        if (lo < cnt && w[lo] < key) ++lo;
         if (lo < cnt && w[lo] == key) at = wi * W + lo;
         pending = false;
       }
@@ -342,9 +346,11 @@ __device__ __forceinline__ void gen_specials(const StepCtx& c, int mode, int32_t
   for (int q = wi + 1; q < nwin && q <= wi + sm.nbuf - 1; ++q) stage_wait(sm, q & (sm.nbuf - 1));
 }
 
-__device__ __forceinline__ int32_t warp_step(const GraphView& g, int64_t t, int64_t v, int k, uint64_t u,
-                                             uint32_t a_p, uint32_t a_q, WarpSmem& sm, int stream_ratio, int lane) {
-  const int64_t bv = g.rp[v], ev = g.rp[v + 1], dv = ev - bv;
+// bv, ev: row bounds of v; bt, et: row bounds of t (k >= 1)
+__device__ __forceinline__ int32_t warp_step(const GraphView& g, int64_t t, int64_t v, int64_t bv, int64_t ev,
+                                             int64_t bt, int64_t et, int k, uint64_t u, uint32_t a_p, uint32_t a_q,
+                                             WarpSmem& sm, int stream_ratio, int lane) {
+  const int64_t dv = ev - bv;
   if (dv == 0) return -1;
   const int32_t* __restrict__ nv = g.col + bv;
   if (k == 0) {
@@ -357,8 +363,7 @@ __device__ __forceinline__ int32_t warp_step(const GraphView& g, int64_t t, int6
   c.g = &g;
   c.bv = bv;
   c.dv = (int)dv;
-  const int64_t bt = g.rp[t];
-  c.dt = (int)(g.rp[t + 1] - bt);
+  c.dt = (int)(et - bt);
   c.nv = nv;
   c.nt = g.col + bt;
   c.t32 = (int32_t)t;
@@ -387,6 +392,7 @@ __device__ __forceinline__ int32_t warp_step(const GraphView& g, int64_t t, int6
 
   SpecialSink sk;
   sk.cnt = 0;
+  sk.ord_t = -1;
   sk.dpart = 0;
   sk.skip = 0;
   sk.cap = sm.cap;  // positions are packed in 30 bits: degrees < 2^30 (checked at load)
@@ -395,6 +401,7 @@ __device__ __forceinline__ int32_t warp_step(const GraphView& g, int64_t t, int6
   uint64_t r = 0, D = 0;
   int prev = -1, chosen = -1;
   bool found = false;
+  const uint64_t d1 = (uint64_t)kAlphaOne - (uint64_t)a_q, d2 = (uint64_t)a_p - (uint64_t)a_q;
   // Pass 1 enumerates every special (and sums the corrections into T); pass 2
   // walks the kept specials in position order.  If the answer lies beyond
   // the kept ones, the specials are enumerated again, keeping the next
@@ -410,6 +417,50 @@ __device__ __forceinline__ int32_t warp_step(const GraphView& g, int64_t t, int6
     }
     __syncwarp();
     __threadfence_block();  // spilled specials are read back by other lanes
+    if (!g.w && sk.cnt <= sk.keep) {
+      // Unweighted, all specials kept: the correction after special m is
+      // (m + 1) d1 plus (d2 - d1) once the x == t special is passed, so
+      // C at special m is known without a scan and the first special with
+      // C > r is found by a 32-way search over the ordinals.
+      auto spec_at = [&](int m) -> int { return (int)((m < sk.cap ? sm.spec[m] : sm.spill[m - sk.cap]) & 0x3fffffffu); };
+      auto Dm = [&](int m) -> uint64_t {
+        return m < 0 ? 0ull : (uint64_t)(m + 1) * d1 + ((sk.ord_t >= 0 && m >= sk.ord_t) ? d2 - d1 : 0ull);
+      };
+      int lo = 0, hi = sk.cnt;  // first m in [lo, hi) with C(pos_m) > r, hi if none
+      while (hi - lo > 0) {
+        const int span = hi - lo;
+        const int step = (span + 31) / 32;
+        const int m = lo + lane * step;
+        const bool ok = m < hi && (uint64_t)a_q * (uint64_t)(spec_at(m) + 1) + Dm(m) > r;
+        const unsigned bal = __ballot_sync(kFull, ok);
+        if (step == 1) {
+          hi = bal ? lo + __ffs(bal) - 1 : hi;
+          break;
+        }
+        if (!bal) {
+          lo += ((hi - 1 - lo) / step) * step + 1;  // past the last probe below hi
+          continue;
+        }
+        const int f = __ffs(bal) - 1;
+        hi = lo + f * step;  // m = hi satisfies
+        if (f > 0) lo = lo + (f - 1) * step + 1;
+      }
+      if (hi < sk.cnt) {
+        const int fpos = spec_at(hi);
+        prev = hi > 0 ? spec_at(hi - 1) : -1;
+        D = Dm(hi - 1);
+        if ((uint64_t)a_q * (uint64_t)fpos + D > r) {
+          chosen = fpos - 1;  // in the gap (prev, fpos - 1]
+        } else {
+          chosen = fpos;
+          found = true;
+        }
+      } else {
+        prev = sk.cnt > 0 ? spec_at(sk.cnt - 1) : -1;
+        D = Dm(sk.cnt - 1);
+      }
+      break;
+    }
     const int n_in = min(sk.cnt - seg, sk.keep);
     for (int c0 = 0; c0 < n_in; c0 += 32) {
       int32_t pos = -1;
@@ -477,20 +528,27 @@ __device__ __forceinline__ int32_t warp_binned_step(const GraphView& g, bool ali
   int32_t x = -1;
   bool small = false;
   uint64_t u = 0;
+  int64_t bv = 0, ev = 0, bt = 0, et = 0;
   if (alive) {
+    // every lane fetches its own walker's row bounds: 32 independent loads
+    bv = g.rp[v];
+    ev = g.rp[v + 1];
+    if (k > 0) {
+      bt = g.rp[t];
+      et = g.rp[t + 1];
+    }
     u = philox_draw(seed, wid, (uint32_t)k);
-    const int64_t dv = g.rp[v + 1] - g.rp[v];
-    small = dv <= thr && (k == 0 || g.rp[t + 1] - g.rp[t] <= thr);
+    small = ev - bv <= thr && (k == 0 || et - bt <= thr);
     if (small) x = thread_step(g, t, v, k, u, a_p, a_q);
   }
   unsigned wm = __ballot_sync(kFull, alive && !small);
   while (wm) {
     const int src = __ffs(wm) - 1;
     wm &= wm - 1;
-    const int64_t tt = __shfl_sync(kFull, t, src);
-    const int64_t vv = __shfl_sync(kFull, v, src);
-    const uint64_t uu = __shfl_sync(kFull, u, src);
-    const int32_t xx = warp_step(g, tt, vv, k, uu, a_p, a_q, sm, stream_ratio, lane);
+    const int32_t xx = warp_step(g, __shfl_sync(kFull, t, src), __shfl_sync(kFull, v, src),
+                                 __shfl_sync(kFull, bv, src), __shfl_sync(kFull, ev, src),
+                                 __shfl_sync(kFull, bt, src), __shfl_sync(kFull, et, src), k,
+                                 __shfl_sync(kFull, u, src), a_p, a_q, sm, stream_ratio, lane);
     if (lane == src) x = xx;
   }
   return x;
