@@ -172,6 +172,26 @@ int n2v_walk(const n2v_graph* g, const int32_t* starts, int64_t n_starts, int32_
              double q, uint64_t seed, int64_t walk_begin, int64_t walk_count, int32_t* walks, void* ws,
              size_t ws_bytes, int variant, void* stream);
 
+/* Allocation-free form of n2v_walk with variant N2V_PERSISTENT, for callers
+ * that cannot allocate device memory (code running inside a memory pool or
+ * arena owned by another runtime, plugins handed only a stream and their
+ * input/output buffers, paths where an allocation could block or fail).
+ * The paper has no counterpart: it only concerns memory management.
+ *
+ * Instead of a caller workspace it uses a scratch array inside the library
+ * (4 MiB of device memory per GPU that loads the library, held until the
+ * process exits).  Arguments and results are those of n2v_walk; the rows are
+ * identical.  The first call on a device looks up that device's scratch
+ * address (cudaGetSymbolAddress): make that first call before any stream
+ * capture.  Every call on a device shares the one scratch array: calls that
+ * overlap on the GPU (other streams, other threads, other graph handles)
+ * race and give wrong rows; serialise them.  The scratch keeps the last
+ * call's contents and each call clears what must start at zero.  Returns
+ * N2V_ERR_NO_MEM when the call would need more than 512 persistent launches
+ * (walk_count / chunk_walkers), otherwise as n2v_walk.  Allocates nothing. */
+int n2v_walk_noalloc(const n2v_graph* g, const int32_t* starts, int64_t n_starts, int32_t r, int32_t l, double p,
+                     double q, uint64_t seed, int64_t walk_begin, int64_t walk_count, int32_t* walks, void* stream);
+
 /* Q16 return parameters exactly as n2v_walk rounds them (host function). */
 int n2v_alpha_q16(double p, double q, uint32_t* a_p, uint32_t* a_q);
 

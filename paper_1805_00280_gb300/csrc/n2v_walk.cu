@@ -431,3 +431,101 @@ int n2v_launch_shape(const n2v_graph* g, int32_t* sms, int32_t* blocks, int32_t*
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the persistent sampler.
+//
+// Some callers cannot allocate device memory at the point where they need
+// walks: code running inside a memory pool or arena that another runtime owns,
+// plugins handed only a stream and the input/output buffers, or real-time
+// paths where an allocation could block or fail.  For them the persistent
+// sampler can run on a scratch area that lives inside this library: a
+// file-scope device array of kNoAllocScratchBytes, reserved on every GPU that
+// loads the library until the process exits.  The scratch holds the work
+// counters (one per persistent launch) and the per-warp spill area for
+// special neighbours; the spill area is only a cache, so a smaller one
+// changes speed, never results.
+
+namespace n2v {
+
+constexpr size_t kNoAllocScratchBytes = (size_t)4 << 20;  // 4 MiB per device
+constexpr size_t kNoAllocCounterBytes = 4096;              // room for 512 launch counters
+constexpr int64_t kNoAllocMaxLaunches = (int64_t)(kNoAllocCounterBytes / sizeof(unsigned long long));
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+// Device address of g_noalloc_scratch per device.  In host code the symbol
+// is only a host-side stand-in; the address comes from cudaGetSymbolAddress
+// with the device current, once per device.
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_addr[kNoAllocMaxDevices];
+
+static int noalloc_scratch(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return N2V_ERR_CUDA;
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return N2V_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return N2V_ERR_CUDA;
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return N2V_OK;
+}
+
+}  // namespace n2v
+
+extern "C" int n2v_walk_noalloc(const n2v_graph* g, const int32_t* starts, int64_t n_starts, int32_t r, int32_t l,
+                                double p, double q, uint64_t seed, int64_t walk_begin, int64_t walk_count,
+                                int32_t* walks, void* stream) {
+  using namespace n2v;
+  if (!g || l < 1 || r < 1 || n_starts < 1 || walk_begin < 0 || walk_count < 0) return N2V_ERR_INVALID_ARG;
+  if (n_starts > INT64_MAX / r) return N2V_ERR_INVALID_ARG;
+  const int64_t total = n_starts * (int64_t)r;
+  if (walk_begin > total || walk_count > total - walk_begin) return N2V_ERR_INVALID_ARG;
+  uint32_t a_p, a_q;
+  if (n2v_alpha_q16(p, q, &a_p, &a_q) != N2V_OK) return N2V_ERR_INVALID_ARG;
+  const uint64_t amax = std::max<uint64_t>(std::max<uint64_t>(a_p, a_q), kAlphaOne);
+  if (g->info.max_wsum > UINT64_MAX / amax) return N2V_ERR_OVERFLOW;
+  if (walk_count == 0) return N2V_OK;
+  if (!starts || !walks) return N2V_ERR_INVALID_ARG;
+  const int64_t chunks = n_chunks(g, walk_count);
+  if (chunks > kNoAllocMaxLaunches) return N2V_ERR_NO_MEM;  // more launch counters than the scratch holds
+  void* scratch = nullptr;
+  int rc = noalloc_scratch(&scratch);
+  if (rc != N2V_OK) return rc;
+
+  LaunchCfg L = resolve_launch(g, N2V_PERSISTENT);
+  const int smem = smem_per_block(L);
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  // the spill area is whatever the scratch has left, shared evenly by the warps
+  const int64_t warps = (int64_t)L.blocks * (L.block_threads / 32);
+  const int64_t per_warp = (int64_t)((kNoAllocScratchBytes - kNoAllocCounterBytes) / sizeof(uint32_t)) / warps;
+  L.spill_specials = (int)std::min<int64_t>(L.spill_specials, per_warp);
+  unsigned long long* counters = (unsigned long long*)scratch;
+  uint32_t* spill = L.spill_specials > 0 ? (uint32_t*)((char*)scratch + kNoAllocCounterBytes) : nullptr;
+
+  cudaStream_t s = (cudaStream_t)stream;
+  // the scratch keeps the previous call's contents: the counters must start at 0
+  if (cudaMemsetAsync(counters, 0, sizeof(unsigned long long) * (size_t)chunks, s) != cudaSuccess)
+    return N2V_ERR_CUDA;
+  WalkJob J;
+  J.starts = starts;
+  J.n_starts = n_starts;
+  J.l = l;
+  J.a_p = a_p;
+  J.a_q = a_q;
+  J.seed = seed;
+  J.status = g->status;
+  const int64_t per = chunks == 1 ? walk_count : g->tune.chunk_walkers;
+  for (int64_t ci = 0; ci < chunks; ++ci) {
+    const int64_t lo = ci * per;
+    J.walk_begin = walk_begin + lo;
+    J.count = std::min<int64_t>(per, walk_count - lo);
+    J.walks = walks + lo * (int64_t)l;
+    k_persistent<<<L.blocks, L.block_threads, smem, s>>>(g->view, J, counters + ci, L, spill);
+  }
+  return cudaGetLastError() == cudaSuccess ? N2V_OK : N2V_ERR_CUDA;
+}

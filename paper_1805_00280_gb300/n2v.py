@@ -87,6 +87,7 @@ def lib() -> ctypes.CDLL:
         L.n2v_walk_ws_bytes.argtypes = [vp, i64, i32, ctypes.c_int, P(sz)]
         L.n2v_walk.argtypes = [vp, vp, i64, i32, i32, dbl, dbl, u64, i64, i64, vp, vp, sz, ctypes.c_int, vp]
         L.n2v_walk_traffic.argtypes = [vp, vp, i64, i64, i64, i32, vp, vp, vp]
+        L.n2v_walk_noalloc.argtypes = [vp, vp, i64, i32, i32, dbl, dbl, u64, i64, i64, vp, vp]
         L.n2v_stream_status.argtypes = [vp, vp]
         L.n2v_strerror.argtypes = [ctypes.c_int]
         L.n2v_strerror.restype = ctypes.c_char_p
@@ -177,6 +178,14 @@ def n2v_walk(handle: int, starts, n_starts: int, r: int, l: int, p: float, q: fl
     rc = lib().n2v_walk(handle, _ptr(starts), n_starts, r, l, p, q, seed, walk_begin, walk_count, _ptr(walks),
                         _ptr(ws), ws_bytes, variant, _stream(stream))
     _check(rc, "n2v_walk")
+
+
+def n2v_walk_noalloc(handle: int, starts, n_starts: int, r: int, l: int, p: float, q: float, seed: int,
+                     walk_begin: int, walk_count: int, walks, stream=None) -> None:
+    """The persistent sampler on the library's own scratch: no workspace, no allocation."""
+    rc = lib().n2v_walk_noalloc(handle, _ptr(starts), n_starts, r, l, p, q, seed, walk_begin, walk_count,
+                                _ptr(walks), _stream(stream))
+    _check(rc, "n2v_walk_noalloc")
 
 
 def n2v_walk_traffic(handle: int, starts, n_starts: int, walk_begin: int, walk_count: int, l: int, walks,
