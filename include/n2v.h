@@ -81,7 +81,9 @@ extern "C" {
 /* ---- tuning ---------------------------------------------------------------- */
 typedef struct n2v_tune {
   int32_t block_threads;   /* threads per block of the binned/persistent kernels (64..1024, x32) */
-  int32_t blocks_per_sm;   /* resident blocks per SM for the persistent grid; 0 = occupancy max */
+  int32_t blocks_per_sm;   /* resident blocks per SM for the persistent grid; 0 = occupancy max.
+                              The persistent kernel is compiled for 2, 3 (default) or 4 resident
+                              256-thread blocks; 2 and >= 4 select those register budgets.      */
   int32_t thread_max_deg;  /* a step runs on one lane when deg(v) and deg(t) are <= this      */
   int32_t smem_specials;   /* per-warp shared-memory slots for the special positions of a step */
   int32_t hub_count;       /* vertices (largest degree first) with a hashed neighbour set     */

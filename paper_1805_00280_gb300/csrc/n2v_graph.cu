@@ -153,8 +153,6 @@ __global__ void k_hub_build(const int64_t* __restrict__ rp, const int32_t* __res
   }
 }
 
-static int cuda_fail(cudaError_t e) { return e == cudaSuccess ? N2V_OK : N2V_ERR_CUDA; }
-
 // Build (or rebuild) the hub cache under g->tune.  Synchronises the stream.
 static int build_hubs(n2v_graph* g, const AuxLayout& L, cudaStream_t s) {
   g->view.hub_of = nullptr;
@@ -247,7 +245,7 @@ void n2v_tune_default(n2v_tune* t) {
   t->hub_min_degree = 256;
   t->chunk_walkers = 0;
   t->hub_budget_mb = 1024;
-  t->stage_window = 512;
+  t->stage_window = 1024;
   t->stream_ratio = 40;
   t->spill_specials = 4096;
   t->stage_buffers = 2;

@@ -57,6 +57,7 @@ struct LaunchCfg {
   int stream_ratio;    // x10
   int spill_specials;  // per warp, in the device workspace (persistent sampler only)
   int stage_buffers;   // staging windows per warp (2 or 4)
+  int minb;            // persistent kernel instance: resident 256-thread blocks per SM it is compiled for
 };
 
 // Shared memory of one warp: four mbarrier slots (32 bytes), the specials

@@ -84,8 +84,10 @@ __global__ void __launch_bounds__(256) k_binned_step(GraphView g, WalkJob J, int
 // time from a device counter and runs them to the end; every step is binned
 // by degree as above.  Walkers are independent (FN-Multi's observation,
 // Section 3.4), so the order in which warps take them does not change any row.
-__global__ void __launch_bounds__(256, 3) k_persistent(GraphView g, WalkJob J, unsigned long long* __restrict__ counter, LaunchCfg L,
-                             uint32_t* __restrict__ spill) {
+template <int MINB>
+__global__ void __launch_bounds__(256, MINB) k_persistent(GraphView g, WalkJob J,
+                                                          unsigned long long* __restrict__ counter, LaunchCfg L,
+                                                          uint32_t* __restrict__ spill) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
@@ -170,6 +172,27 @@ __global__ void k_traffic(const int64_t* __restrict__ rp, int weighted, const in
 
 static int smem_per_block(const LaunchCfg& c) { return (c.block_threads / 32) * warp_smem_bytes(c); }
 
+// The persistent kernel is compiled for 2, 3 or 4 resident 256-thread blocks
+// per SM (128, 80 or 64 registers per thread); blocks_per_sm picks one.
+static int persistent_minb(const n2v_tune& t) { return t.blocks_per_sm >= 4 ? 4 : (t.blocks_per_sm == 2 ? 2 : 3); }
+
+static const void* persistent_fn(int minb) {
+  switch (minb) {
+    case 2: return (const void*)k_persistent<2>;
+    case 4: return (const void*)k_persistent<4>;
+    default: return (const void*)k_persistent<3>;
+  }
+}
+
+static void launch_persistent(const LaunchCfg& L, int smem, cudaStream_t s, const GraphView& g, const WalkJob& J,
+                              unsigned long long* counter, uint32_t* spill) {
+  switch (L.minb) {
+    case 2: k_persistent<2><<<L.blocks, L.block_threads, smem, s>>>(g, J, counter, L, spill); break;
+    case 4: k_persistent<4><<<L.blocks, L.block_threads, smem, s>>>(g, J, counter, L, spill); break;
+    default: k_persistent<3><<<L.blocks, L.block_threads, smem, s>>>(g, J, counter, L, spill); break;
+  }
+}
+
 LaunchCfg resolve_launch(const n2v_graph* g, int variant) {
   LaunchCfg c{};
   c.block_threads = g->tune.block_threads;
@@ -179,11 +202,12 @@ LaunchCfg resolve_launch(const n2v_graph* g, int variant) {
   c.stream_ratio = g->tune.stream_ratio;
   c.spill_specials = g->tune.spill_specials;
   c.stage_buffers = g->tune.stage_buffers;
+  c.minb = persistent_minb(g->tune);
   const int smem = smem_per_block(c);
   int per_sm = g->tune.blocks_per_sm;
   if (per_sm <= 0) {
     per_sm = 1;
-    const void* fn = variant == N2V_PERSISTENT ? (const void*)k_persistent : (const void*)k_binned_step;
+    const void* fn = variant == N2V_PERSISTENT ? persistent_fn(c.minb) : (const void*)k_binned_step;
     if (smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, c.block_threads, smem) == cudaSuccess && occ > 0)
@@ -244,7 +268,7 @@ static cudaError_t issue(const n2v_graph* g, const WalkCall& c, cudaStream_t s) 
     return cudaGetLastError();
   }
   // persistent
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (smem > 48 * 1024) cudaFuncSetAttribute(persistent_fn(L.minb), cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   const int64_t chunks = n_chunks(g, c.count);
   unsigned long long* counters = (unsigned long long*)c.ws;
   cudaError_t e = cudaMemsetAsync(counters, 0, sizeof(unsigned long long) * (size_t)chunks, s);
@@ -257,7 +281,7 @@ static cudaError_t issue(const n2v_graph* g, const WalkCall& c, cudaStream_t s) 
     Jc.walk_begin = c.walk_begin + lo;
     Jc.count = std::min<int64_t>(per, c.count - lo);
     Jc.walks = c.walks + lo * (int64_t)c.l;
-    k_persistent<<<L.blocks, L.block_threads, smem, s>>>(g->view, Jc, counters + ci, L, spill);
+    launch_persistent(L, smem, s, g->view, Jc, counters + ci, spill);
   }
   return cudaGetLastError();
 }
@@ -499,7 +523,7 @@ extern "C" int n2v_walk_noalloc(const n2v_graph* g, const int32_t* starts, int64
 
   LaunchCfg L = resolve_launch(g, N2V_PERSISTENT);
   const int smem = smem_per_block(L);
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (smem > 48 * 1024) cudaFuncSetAttribute(persistent_fn(L.minb), cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   // the spill area is whatever the scratch has left, shared evenly by the warps
   const int64_t warps = (int64_t)L.blocks * (L.block_threads / 32);
   const int64_t per_warp = (int64_t)((kNoAllocScratchBytes - kNoAllocCounterBytes) / sizeof(uint32_t)) / warps;
@@ -525,7 +549,7 @@ extern "C" int n2v_walk_noalloc(const n2v_graph* g, const int32_t* starts, int64
     J.walk_begin = walk_begin + lo;
     J.count = std::min<int64_t>(per, walk_count - lo);
     J.walks = walks + lo * (int64_t)l;
-    k_persistent<<<L.blocks, L.block_threads, smem, s>>>(g->view, J, counters + ci, L, spill);
+    launch_persistent(L, smem, s, g->view, J, counters + ci, spill);
   }
   return cudaGetLastError() == cudaSuccess ? N2V_OK : N2V_ERR_CUDA;
 }
