@@ -211,6 +211,80 @@ int n2v_walk_traffic(const n2v_graph* g, const int32_t* starts, int64_t n_starts
  * stream reports a CUDA error. */
 int n2v_stream_status(const n2v_graph* g, void* stream);
 
+/* ---- autotuner -------------------------------------------------------------- */
+
+/* Workspace bytes n2v_autotune needs for a sample of `sample` walks of length l. */
+int n2v_autotune_ws_bytes(const n2v_graph* g, int64_t sample, int32_t l, size_t* bytes);
+
+/* Pick the tuning of the persistent sampler for this graph and job shape:
+ * a coordinate descent over stage_window, blocks_per_sm, stream_ratio,
+ * thread_max_deg, stage_buffers and (if the graph was loaded with hubs)
+ * hub_count, each candidate timed with CUDA events on walks [0, sample) of
+ * the job "one walk from each of starts[0..sample)" (the caller should pass a
+ * representative random sample of its start vertices).  Every tuning gives
+ * the same rows, so only time is compared.  `walks` (device int32
+ * [sample][l]) and `ws` (n2v_autotune_ws_bytes) are scratch.  Synchronises
+ * `stream`.  On success the best tuning is applied to g and returned in
+ * *best (and its sample time in *best_ms). */
+int n2v_autotune(n2v_graph* g, const int32_t* starts, int64_t n_starts, int32_t l, double p, double q, uint64_t seed,
+                 int64_t sample, int32_t* walks, void* ws, size_t ws_bytes, void* stream, n2v_tune* best,
+                 float* best_ms);
+
+/* ---- serving: continuous batching of walk jobs ------------------------------- */
+/* A job: one walk (r = 1) of length l from each of its n_starts start vertices
+ * (repeats allowed), with its own p, q and seed.  Its rows are bit-identical
+ * to n2v_walk(g, starts, n_starts, 1, l, p, q, seed, 0, n_starts, ...),
+ * whatever other jobs it is mixed with.  There is no serving in the paper;
+ * the job granularity plays the role of FN-Multi's rounds (Section 3.4). */
+typedef struct n2v_job {
+  const int32_t* starts;  /* HOST int32 [n_starts]; copied at submit */
+  int64_t n_starts;
+  int32_t l;
+  int32_t reserved0;
+  double p, q;
+  uint64_t seed;
+} n2v_job;
+
+typedef struct n2v_serve_cfg {
+  int64_t tick_walkers;      /* walkers per tick (one persistent launch)            */
+  int32_t max_jobs_per_tick; /* jobs mixed into one tick                            */
+  int32_t spill_specials;    /* per-warp spill slots (inside the arena)             */
+  int64_t min_share;         /* smallest share of a tick given to one job           */
+  int64_t reserved[4];
+} n2v_serve_cfg;
+
+typedef struct n2v_serve_stats_t {
+  int64_t queued, active, arena_used, arena_bytes, ticks;
+} n2v_serve_stats_t;
+
+typedef struct n2v_server n2v_server; /* opaque */
+
+void n2v_serve_cfg_default(n2v_serve_cfg* cfg);
+
+/* A server over a loaded graph.  `arena` (device, caller-owned, 256-byte
+ * aligned) holds the tick tables and, for every admitted job, its start
+ * vertices and output rows: a job is admitted (in submission order) when its
+ * bytes, 4*n_starts + 4*n_starts*l rounded up to 256, fit in the free part of
+ * the arena -- admission by free HBM.  All device work goes on `stream`. */
+int n2v_serve_create(const n2v_graph* g, void* arena, size_t arena_bytes, const n2v_serve_cfg* cfg, void* stream,
+                     n2v_server** out);
+/* Queue a job (host call, returns at once); *job_id identifies it. */
+int n2v_serve_submit(n2v_server* s, const n2v_job* job, int64_t* job_id);
+/* Non-blocking scheduler step: retire ticks the GPU finished, admit queued
+ * jobs that fit, and, unless a tick is already queued, launch the next tick:
+ * one persistent launch over up to tick_walkers walkers drawn from every
+ * active job (equal shares).  *launched = 1 when a tick was launched. */
+int n2v_serve_step(n2v_server* s, int* launched);
+/* Up to max_ids finished job ids, oldest first. */
+int n2v_serve_poll(n2v_server* s, int64_t* ids, int max_ids, int* n);
+/* Device pointer to a finished job's rows, int32 [n_starts][l]. */
+int n2v_serve_job_rows(n2v_server* s, int64_t job_id, int32_t** rows);
+/* Give a finished job's arena space back (its rows become invalid). */
+int n2v_serve_release(n2v_server* s, int64_t job_id);
+int n2v_serve_stats(n2v_server* s, n2v_serve_stats_t* st);
+/* Destroy the server (synchronise the stream first; the arena stays the caller's). */
+void n2v_serve_destroy(n2v_server* s);
+
 /* Static text for a status code. */
 const char* n2v_strerror(int code);
 

@@ -339,8 +339,10 @@ int n2v_graph_retune(n2v_graph* g, const n2v_tune* t, void* stream) {
   AuxLayout L = aux_layout(g->n, g->nnz, g->weighted, *t);
   if (L.total > g->aux_bytes) return N2V_ERR_NO_MEM;
   free_graph_cache(g);
+  const bool same_hubs = t->hub_count == g->tune.hub_count && t->hub_min_degree == g->tune.hub_min_degree &&
+                         t->hub_budget_mb == g->tune.hub_budget_mb;
   g->tune = *t;
-  return build_hubs(g, L, (cudaStream_t)stream);
+  return same_hubs ? N2V_OK : build_hubs(g, L, (cudaStream_t)stream);
 }
 
 void n2v_graph_free(n2v_graph* g) {

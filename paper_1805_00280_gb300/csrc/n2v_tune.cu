@@ -1,0 +1,112 @@
+// Autotuner of the persistent sampler: a coordinate descent over its
+// tunables, each candidate timed with CUDA events on a sample of the job.
+// Every tuning gives the same rows (the step is exact on every code path), so
+// only speed is compared.
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "n2v_internal.cuh"
+
+namespace n2v {
+
+struct Axis {
+  int32_t n2v_tune::*field;
+  std::vector<int32_t> values;
+};
+
+static size_t ws_for(const n2v_graph* g, int64_t sample, int32_t l, int blocks_per_sm, int spill) {
+  const int64_t chunks = g->tune.chunk_walkers > 0 ? (sample + g->tune.chunk_walkers - 1) / g->tune.chunk_walkers : 1;
+  size_t b = ((sizeof(unsigned long long) * (size_t)chunks) + 255) & ~(size_t)255;
+  b += sizeof(uint32_t) * (size_t)g->sms * (size_t)blocks_per_sm * (size_t)(g->tune.block_threads / 32) * (size_t)spill;
+  (void)l;
+  return b;
+}
+
+}  // namespace n2v
+
+using namespace n2v;
+
+extern "C" {
+
+int n2v_autotune_ws_bytes(const n2v_graph* g, int64_t sample, int32_t l, size_t* bytes) {
+  if (!g || !bytes || sample < 1 || l < 1) return N2V_ERR_INVALID_ARG;
+  // the largest candidate grid: 4 resident blocks per SM (or the caller's larger choice)
+  *bytes = ws_for(g, sample, l, std::max(4, g->tune.blocks_per_sm), g->tune.spill_specials);
+  return N2V_OK;
+}
+
+int n2v_autotune(n2v_graph* g, const int32_t* starts, int64_t n_starts, int32_t l, double p, double q, uint64_t seed,
+                 int64_t sample, int32_t* walks, void* ws, size_t ws_bytes, void* stream, n2v_tune* best,
+                 float* best_ms) {
+  if (!g || !starts || n_starts < 1 || l < 1 || sample < 1 || sample > n_starts || !walks || !ws) return N2V_ERR_INVALID_ARG;
+  size_t need = 0;
+  int rc = n2v_autotune_ws_bytes(g, sample, l, &need);
+  if (rc != N2V_OK) return rc;
+  if (ws_bytes < need) return N2V_ERR_NO_MEM;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return N2V_ERR_CUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return N2V_ERR_CUDA;
+  }
+  const n2v_tune start = g->tune;
+  // one timed run of the sample (after one untimed run) under tuning t
+  auto measure = [&](const n2v_tune& t, float* ms) -> int {
+    int r0 = n2v_graph_retune(g, &t, stream);
+    if (r0 != N2V_OK) return r0;
+    for (int rep = 0; rep < 2; ++rep) {
+      if (rep == 1 && cudaEventRecord(e0, s) != cudaSuccess) return N2V_ERR_CUDA;
+      r0 = n2v_walk(g, starts, n_starts, 1, l, p, q, seed, 0, sample, walks, ws, ws_bytes, N2V_PERSISTENT, stream);
+      if (r0 != N2V_OK) return r0;
+    }
+    if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) return N2V_ERR_CUDA;
+    if (cudaEventElapsedTime(ms, e0, e1) != cudaSuccess) return N2V_ERR_CUDA;
+    return n2v_stream_status(g, stream);
+  };
+
+  std::vector<Axis> axes;
+  axes.push_back({&n2v_tune::stage_window, {512, 1024, 256}});
+  axes.push_back({&n2v_tune::blocks_per_sm, {3, 4}});
+  axes.push_back({&n2v_tune::stream_ratio, {15, 40, 100}});
+  axes.push_back({&n2v_tune::thread_max_deg, {0, 16, 48}});
+  axes.push_back({&n2v_tune::stage_buffers, {2, 4}});
+  if (start.hub_count > 0) axes.push_back({&n2v_tune::hub_count, {0, start.hub_count}});
+
+  n2v_tune cur = start;
+  if (cur.blocks_per_sm <= 0) cur.blocks_per_sm = 3;
+  float cur_ms = 0.f;
+  rc = measure(cur, &cur_ms);
+  for (size_t a = 0; a < axes.size() && rc == N2V_OK; ++a) {
+    for (int32_t val : axes[a].values) {
+      if (cur.*(axes[a].field) == val) continue;
+      n2v_tune cand = cur;
+      cand.*(axes[a].field) = val;
+      // 4 windows of 1024 do not fit beside 3 resident blocks: skip that corner
+      if (cand.stage_buffers * (cand.stage_window + 8) * 4 * (cand.block_threads / 32) * cand.blocks_per_sm > 200 * 1024)
+        continue;
+      float ms = 0.f;
+      rc = measure(cand, &ms);
+      if (rc != N2V_OK) break;
+      if (ms < cur_ms) {
+        cur = cand;
+        cur_ms = ms;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != N2V_OK) {
+    n2v_graph_retune(g, &start, stream);
+    return rc;
+  }
+  rc = n2v_graph_retune(g, &cur, stream);
+  if (best) *best = cur;
+  if (best_ms) *best_ms = cur_ms;
+  return rc;
+}
+
+}  // extern "C"

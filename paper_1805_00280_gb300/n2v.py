@@ -61,6 +61,23 @@ class n2v_graph_info(ctypes.Structure):
                 ("deg_hist", ctypes.c_int64 * 34)]
 
 
+class n2v_job(ctypes.Structure):
+    _fields_ = [("starts", ctypes.c_void_p), ("n_starts", ctypes.c_int64), ("l", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32), ("p", ctypes.c_double), ("q", ctypes.c_double),
+                ("seed", ctypes.c_uint64)]
+
+
+class n2v_serve_cfg(ctypes.Structure):
+    _fields_ = [("tick_walkers", ctypes.c_int64), ("max_jobs_per_tick", ctypes.c_int32),
+                ("spill_specials", ctypes.c_int32), ("min_share", ctypes.c_int64),
+                ("reserved", ctypes.c_int64 * 4)]
+
+
+class n2v_serve_stats_t(ctypes.Structure):
+    _fields_ = [("queued", ctypes.c_int64), ("active", ctypes.c_int64), ("arena_used", ctypes.c_int64),
+                ("arena_bytes", ctypes.c_int64), ("ticks", ctypes.c_int64)]
+
+
 _LIB = None
 
 
@@ -92,6 +109,20 @@ def lib() -> ctypes.CDLL:
         L.n2v_strerror.argtypes = [ctypes.c_int]
         L.n2v_strerror.restype = ctypes.c_char_p
         L.n2v_launch_shape.argtypes = [vp, P(i32), P(i32), P(i32)]
+        L.n2v_serve_cfg_default.argtypes = [P(n2v_serve_cfg)]
+        L.n2v_serve_cfg_default.restype = None
+        L.n2v_serve_create.argtypes = [vp, vp, sz, P(n2v_serve_cfg), vp, P(vp)]
+        L.n2v_serve_submit.argtypes = [vp, P(n2v_job), P(i64)]
+        L.n2v_serve_step.argtypes = [vp, P(ctypes.c_int)]
+        L.n2v_serve_poll.argtypes = [vp, vp, ctypes.c_int, P(ctypes.c_int)]
+        L.n2v_serve_job_rows.argtypes = [vp, i64, P(vp)]
+        L.n2v_serve_release.argtypes = [vp, i64]
+        L.n2v_serve_stats.argtypes = [vp, P(n2v_serve_stats_t)]
+        L.n2v_serve_destroy.argtypes = [vp]
+        L.n2v_serve_destroy.restype = None
+        L.n2v_autotune_ws_bytes.argtypes = [vp, i64, i32, P(sz)]
+        L.n2v_autotune.argtypes = [vp, vp, i64, i32, dbl, dbl, u64, i64, vp, vp, sz, vp, P(n2v_tune),
+                                   P(ctypes.c_float)]
         _LIB = L
     return _LIB
 
@@ -204,6 +235,76 @@ def n2v_launch_shape(handle: int) -> tuple[int, int, int]:
     return a.value, b.value, c.value
 
 
+def n2v_autotune_ws_bytes(handle: int, sample: int, l: int) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().n2v_autotune_ws_bytes(handle, sample, l, ctypes.byref(b)), "n2v_autotune_ws_bytes")
+    return b.value
+
+
+def n2v_autotune(handle: int, starts, n_starts: int, l: int, p: float, q: float, seed: int, sample: int, walks,
+                 ws, stream=None) -> tuple[n2v_tune, float]:
+    best, ms = n2v_tune(), ctypes.c_float()
+    ws_bytes = ws.numel() * ws.element_size()
+    _check(lib().n2v_autotune(handle, _ptr(starts), n_starts, l, p, q, seed, sample, _ptr(walks), _ptr(ws), ws_bytes,
+                              _stream(stream), ctypes.byref(best), ctypes.byref(ms)), "n2v_autotune")
+    return best, ms.value
+
+
+def n2v_serve_cfg_default() -> n2v_serve_cfg:
+    c = n2v_serve_cfg()
+    lib().n2v_serve_cfg_default(ctypes.byref(c))
+    return c
+
+
+def n2v_serve_create(handle: int, arena, cfg: n2v_serve_cfg | None = None, stream=None) -> int:
+    out = ctypes.c_void_p()
+    nbytes = arena.numel() * arena.element_size()
+    _check(lib().n2v_serve_create(handle, _ptr(arena), nbytes, ctypes.byref(cfg) if cfg else None, _stream(stream),
+                                  ctypes.byref(out)), "n2v_serve_create")
+    return out.value
+
+
+def n2v_serve_submit(server: int, starts: np.ndarray, l: int, p: float, q: float, seed: int) -> int:
+    starts = np.ascontiguousarray(starts, dtype=np.int32)
+    job = n2v_job(starts.ctypes.data, starts.shape[0], l, 0, p, q, seed)
+    jid = ctypes.c_int64()
+    _check(lib().n2v_serve_submit(server, ctypes.byref(job), ctypes.byref(jid)), "n2v_serve_submit")
+    return jid.value
+
+
+def n2v_serve_step(server: int) -> bool:
+    launched = ctypes.c_int()
+    _check(lib().n2v_serve_step(server, ctypes.byref(launched)), "n2v_serve_step")
+    return bool(launched.value)
+
+
+def n2v_serve_poll(server: int, max_ids: int = 4096) -> list[int]:
+    ids = np.zeros(max_ids, dtype=np.int64)
+    n = ctypes.c_int()
+    _check(lib().n2v_serve_poll(server, ids.ctypes.data, max_ids, ctypes.byref(n)), "n2v_serve_poll")
+    return ids[: n.value].tolist()
+
+
+def n2v_serve_job_rows(server: int, job_id: int) -> int:
+    p = ctypes.c_void_p()
+    _check(lib().n2v_serve_job_rows(server, job_id, ctypes.byref(p)), "n2v_serve_job_rows")
+    return p.value
+
+
+def n2v_serve_release(server: int, job_id: int) -> None:
+    _check(lib().n2v_serve_release(server, job_id), "n2v_serve_release")
+
+
+def n2v_serve_stats(server: int) -> dict:
+    st = n2v_serve_stats_t()
+    _check(lib().n2v_serve_stats(server, ctypes.byref(st)), "n2v_serve_stats")
+    return {f: getattr(st, f) for f, _ in st._fields_}
+
+
+def n2v_serve_destroy(server: int) -> None:
+    lib().n2v_serve_destroy(server)
+
+
 # --------------------------------------------------------------------------
 # conveniences
 
@@ -279,6 +380,22 @@ def walk(graph: Graph, starts, r: int, l: int, p: float, q: float, seed: int, va
     return out
 
 
+def autotune(graph: Graph, starts, l: int, p: float, q: float, seed: int = 1, sample: int = 1 << 16,
+             rng_seed: int = 0, stream=None) -> tuple[n2v_tune, float]:
+    """Tune the persistent sampler on a random sample of the given start vertices (applied to graph)."""
+    dev = graph.row_ptr.device
+    starts = torch.as_tensor(starts, dtype=torch.int32).to(dev)
+    gen = torch.Generator(device="cpu").manual_seed(rng_seed)
+    pick = torch.randperm(starts.numel(), generator=gen)[: min(sample, starts.numel())].to(dev)
+    sub = starts[pick].contiguous()
+    walks = torch.empty((sub.numel(), l), dtype=torch.int32, device=dev)
+    need = n2v_autotune_ws_bytes(graph.handle, sub.numel(), l)
+    ws = torch.empty(need // 8 + 32, dtype=torch.int64, device=dev)
+    best, ms = n2v_autotune(graph.handle, sub, sub.numel(), l, p, q, seed, sub.numel(), walks, ws, stream)
+    graph.tune = best
+    return best, ms
+
+
 def traffic(graph: Graph, starts, walk_begin: int, walks: torch.Tensor, stream=None) -> tuple[int, int]:
     """(real transitions, model adjacency bytes) of the rows in ``walks`` (synchronises)."""
     dev = graph.row_ptr.device
@@ -288,3 +405,52 @@ def traffic(graph: Graph, starts, walk_begin: int, walks: torch.Tensor, stream=N
                      int(walks.shape[1]), walks, out2, stream)
     o = out2.cpu()
     return int(o[0]), int(o[1])
+
+
+class Server:
+    """Continuous-batching walk server over a Graph; the arena is a torch buffer."""
+
+    def __init__(self, graph: Graph, arena_bytes: int, cfg: n2v_serve_cfg | None = None, stream=None):
+        self.graph = graph
+        self.arena = torch.empty(arena_bytes // 8 + 64, dtype=torch.int64, device=graph.row_ptr.device)
+        self.stream = stream
+        self.handle = n2v_serve_create(graph.handle, self.arena, cfg, stream)
+        self.jobs: dict[int, tuple[int, int]] = {}
+
+    def submit(self, starts, l: int, p: float, q: float, seed: int) -> int:
+        starts = np.ascontiguousarray(starts, dtype=np.int32)
+        jid = n2v_serve_submit(self.handle, starts, l, p, q, seed)
+        self.jobs[jid] = (starts.shape[0], l)
+        return jid
+
+    def step(self) -> bool:
+        return n2v_serve_step(self.handle)
+
+    def poll(self) -> list[int]:
+        return n2v_serve_poll(self.handle)
+
+    def rows(self, jid: int) -> torch.Tensor:
+        """A view of a finished job's rows inside the arena (valid until release)."""
+        ptr = n2v_serve_job_rows(self.handle, jid)
+        n, l = self.jobs[jid]
+        off = (ptr - self.arena.data_ptr()) // 4
+        return self.arena.view(torch.int32)[off: off + n * l].view(n, l)
+
+    def release(self, jid: int) -> None:
+        n2v_serve_release(self.handle, jid)
+        self.jobs.pop(jid, None)
+
+    def stats(self) -> dict:
+        return n2v_serve_stats(self.handle)
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            torch.cuda.synchronize()
+            n2v_serve_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
