@@ -51,7 +51,7 @@ def make_jobs(n_vertices, count, seed):
     rng = np.random.default_rng(seed)
     jobs = []
     for j in range(count):
-        size = int(np.exp(rng.uniform(0, np.log(6000))))
+        size = int(np.exp(rng.uniform(0, np.log(3000))))
         starts = rng.integers(0, n_vertices, size=size).astype(np.int32)
         l = int(rng.choice([10, 20, 40, 80]))
         p = q16(float(np.exp(rng.uniform(np.log(0.25), np.log(4)))))
@@ -68,13 +68,14 @@ def test_serving_mix_equals_alone(rmat15):
     cfg.tick_walkers = 8192
     cfg.min_share = 512
     cfg.spill_specials = 32
-    # a small arena: admission has to wait for memory to free up
-    srv = n2v.Server(graph, 6 << 20, cfg)
+    # a small arena (about 2.4 MB for jobs after the tick tables): admission has
+    # to wait for memory to free up
+    srv = n2v.Server(graph, 3 << 20, cfg)
     ids, order = {}, []
     saw_queue = False
     for i, (starts, l, p, q, seed) in enumerate(jobs):
         ids[srv.submit(starts, l, p, q, seed)] = i
-        if i % 6 == 5:  # jobs keep arriving while earlier ones run
+        if i % 12 == 11:  # jobs keep arriving while earlier ones run
             srv.step()
             saw_queue |= srv.stats()["queued"] > 0
     done = 0
