@@ -54,7 +54,19 @@ def parse_args():
     ap.add_argument("--walk-count", type=int, default=0, help="limit walks per launch (profiling cases)")
     ap.add_argument("--compare-rounds", type=int, default=1,
                     help="the compared variants run the first R rounds (every start vertex R times)")
+    ap.add_argument("--compare-walks", type=int, default=1 << 22, help="cap on the walks of the compared variants")
+    ap.add_argument("--cuda-graph", type=int, default=-1, help="record the launches as a CUDA graph (-1: per workload)")
+    ap.add_argument("--autotune", type=int, default=1, help="tune the persistent sampler on a sample first")
+    ap.add_argument("--jobs", type=int, default=10_000, help="serving workload: number of jobs")
+    ap.add_argument("--load", type=float, default=0.8, help="serving: arrival rate as a fraction of capacity")
     return ap.parse_args()
+
+
+# workload-specific defaults: the scale-26 graph runs in 8M-walker launches
+# (FN-Multi-style rounds) recorded as one CUDA graph
+WORKLOAD_DEFAULTS = {
+    "rmat26": {"tune": {"chunk_walkers": 1 << 23}, "cuda_graph": 1},
+}
 
 
 def dist_env():
@@ -196,6 +208,30 @@ def run_reference(args):
     g = G.workload_graph(wl.name)
     starts = np.arange(g.n, dtype=np.int32)
     threads = os.cpu_count() or 1
+    if not pq:  # serving workload: the oracle on the first jobs of the same mix
+        import oracle
+
+        jobs = serving_jobs(g.n, min(args.jobs, 64))
+        t0, st, used = time.perf_counter(), 0, 0
+        for jb in jobs:
+            s_np = G.uniform(jb["seed"], jb["stream"], g.n, jb["size"]).astype(np.int32)
+            ids = np.arange(min(jb["size"], 2048))
+            rows = oracle.walk(g.row_ptr, g.col, g.w, s_np, jb["l"], jb["p"], jb["q"], jb["seed"], ids, threads=threads)
+            st += int((rows >= 0).sum())
+            used += 1
+            if time.perf_counter() - t0 > 60:
+                break
+        dt = time.perf_counter() - t0
+        value = st / dt
+        print(json.dumps({"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+                          "steps": 1, "warmup": 0, "ms_per_step": dt * 1e3, "higher_is_better": True,
+                          "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+                          "config": {"workload": wl.name, "jobs_sampled": used},
+                          "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                           "sample": f"first 2048 walks of each of the first {used} jobs"},
+                          "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
+              flush=True)
+        return
     per_step_budget = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
     # size the per-step sample once
     steps_done, t_done, desc, _, _ = cpu_oracle_sample(g, starts, r, wl.l, pq, wl.seed, per_step_budget, threads,
@@ -252,13 +288,26 @@ def run_ours(args):
             torch.distributed.barrier()
 
     wl, pq, r = workload_params(args)
+    wdef = WORKLOAD_DEFAULTS.get(wl.name, {})
     t0 = time.perf_counter()
     g = G.workload_graph(wl.name)
     gen_s = time.perf_counter() - t0
-    tune = n2v.default_tune(**(json.loads(args.tune) if args.tune else {}))
+    tune_kw = dict(wdef.get("tune", {}))
+    tune_kw.update(json.loads(args.tune) if args.tune else {})
+    tune = n2v.default_tune(**tune_kw)
+    cuda_graph = bool(wdef.get("cuda_graph", 0)) if args.cuda_graph < 0 else bool(args.cuda_graph)
+    stream = torch.cuda.Stream(dev)  # a side stream: CUDA graphs cannot record the legacy stream
+    torch.cuda.set_stream(stream)
     t0 = time.perf_counter()
     graph = n2v.Graph.from_csr(g, tune=tune, device=dev)
     load_s = time.perf_counter() - t0
+    tuned = None
+    if args.autotune and args.variant == "persistent":
+        t0 = time.perf_counter()
+        best, ms = n2v.autotune(graph, np.arange(g.n, dtype=np.int32), wl.l, pq[0][0], pq[0][1], wl.seed,
+                                sample=1 << 16, stream=stream)
+        tuned = {"tune": best.as_dict(), "sample_ms": round(ms, 3), "tune_s": round(time.perf_counter() - t0, 2)}
+        tune = best
     info = graph.info()
     l = wl.l
     n_start = g.n
@@ -269,10 +318,9 @@ def run_ours(args):
     walk_begin = rank * W
     starts = torch.arange(n_start, dtype=torch.int32, device=dev)
     outs = [torch.empty((W, l), dtype=torch.int32, device=dev) for _ in pq]
-    variant = n2v.VARIANTS[args.variant]
+    variant = n2v.VARIANTS[args.variant] | (n2v.N2V_FLAG_CUDA_GRAPH if cuda_graph else 0)
     ws_bytes = max(n2v.n2v_walk_ws_bytes(graph.handle, W, l, variant), 256)
     ws = torch.empty(ws_bytes // 8 + 32, dtype=torch.int64, device=dev)
-    stream = torch.cuda.current_stream(dev)
     flush = torch.empty(max(args.flush_mb, 1) * (1 << 20) // 4, dtype=torch.int32, device=dev)
 
     def launch(i, v=variant, out=None):
@@ -339,7 +387,7 @@ def run_ours(args):
     # ---- the other variants, once each on the first rounds of walk ids (every start vertex
     #      `compare_rounds` times), beside the main variant on the same rows
     compare = {}
-    Wc = min(W, n_start * max(1, args.compare_rounds))
+    Wc = min(W, n_start * max(1, args.compare_rounds), args.compare_walks)
     names = [v for v in args.compare.split(",") if v and v != args.variant]
     if names:
         tmp = torch.empty((Wc, l), dtype=torch.int32, device=dev)
@@ -424,7 +472,8 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": wl.name, "desc": wl.note, "n": g.n, "nnz": g.nnz, "weighted": g.w is not None,
                    "r": r, "l": l, "pq": pq, "walks_per_gpu": W, "variant": args.variant,
-                   "tune": tune.as_dict(), "hubs": info.hub_count, "hub_min_degree": info.hub_min_degree,
+                   "tune": tune.as_dict(), "autotune": tuned, "cuda_graph": cuda_graph,
+                   "hubs": info.hub_count, "hub_min_degree": info.hub_min_degree,
                    "max_degree": info.max_degree,
                    "l2": f"flushed between steps ({args.flush_mb} MB write); output {4 * W * l * len(pq) >> 20} MB",
                    "gen_s": round(gen_s, 2), "load_s": round(load_s, 3)},
@@ -434,7 +483,8 @@ def run_ours(args):
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": args.steps * len(pq) * (1 if args.variant == "persistent" else l),
+        "gpu_launches": args.steps * len(pq) * (
+            (-(-W // tune.chunk_walkers) if tune.chunk_walkers > 0 else 1) if args.variant == "persistent" else l),
         "clocks": clk,
         "compare": compare,
         "parity": parity,
@@ -447,10 +497,152 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+# --------------------------------------------------------------------------
+# serving: continuous batching of walk jobs with Poisson arrivals
+
+def serving_jobs(n_vertices: int, count: int, run_seed: int = 1):
+    """The job mix: start-set size log-uniform in [1, 2^20] (uniform vertices, with
+    replacement), l uniform in {10, 20, 40, 80}, p and q log-uniform in [0.25, 4]
+    quantised to Q16, seed = hash(run seed, job id)."""
+    import numpy as np
+
+    from paper_1805_00280_gb300 import graphs as G
+
+    raw = G.raw64(run_seed, 77, 4 * count).reshape(count, 4)
+    u = (raw >> np.uint64(11)).astype(np.float64) / float(1 << 53)
+    jobs = []
+    for j in range(count):
+        size = max(1, min(1 << 20, int(np.exp(u[j, 0] * np.log(1 << 20)))))
+        l = [10, 20, 40, 80][int(raw[j, 1] % np.uint64(4))]
+        p = round(float(np.exp(np.log(0.25) + u[j, 2] * np.log(16.0))) * 65536) / 65536
+        q = round(float(np.exp(np.log(0.25) + u[j, 3] * np.log(16.0))) * 65536) / 65536
+        jobs.append({"size": size, "l": l, "p": p, "q": q, "seed": int(G.raw64(run_seed, 1000 + j, 1)[0]),
+                     "stream": 5000 + j})
+    return jobs
+
+
+def run_serving(args):
+    import numpy as np
+    import torch
+
+    from paper_1805_00280_gb300 import graphs as G
+    from paper_1805_00280_gb300 import n2v
+
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    wl = G.WORKLOADS[args.workload]
+    t0 = time.perf_counter()
+    g = G.workload_graph(wl.name)
+    gen_s = time.perf_counter() - t0
+    graph = n2v.Graph.from_csr(g, device=dev)
+    best, _ = n2v.autotune(graph, np.arange(g.n, dtype=np.int32), 40, 1.0, 1.0, 1, sample=1 << 16, stream=stream)
+    jobs = serving_jobs(g.n, args.jobs)
+    for jb in jobs:
+        jb["starts"] = G.uniform(jb["seed"], jb["stream"], g.n, jb["size"]).astype(np.int32)
+    free, total = torch.cuda.mem_get_info(dev)
+    arena_bytes = int(min(free * 0.6, 96 << 30))  # admission by free HBM: the arena is what is free
+    cfg = n2v.n2v_serve_cfg_default()
+    srv = n2v.Server(graph, arena_bytes, cfg, stream)
+    counted = torch.zeros((), dtype=torch.int64, device=dev)
+
+    def run_batch(sel, arrivals=None):
+        """Serve jobs `sel`; arrivals[i] = submit time offset (None: all at t=0).
+        Returns (makespan_s, latencies_s, real transitions)."""
+        counted.zero_()
+        sub_t, lat = {}, []
+        pending = sorted(range(len(sel)), key=lambda i: 0.0 if arrivals is None else arrivals[i])
+        pi = 0
+        t_start = time.perf_counter()
+        done = 0
+        while done < len(sel):
+            now = time.perf_counter() - t_start
+            while pi < len(pending) and (arrivals is None or arrivals[pending[pi]] <= now):
+                jb = jobs[sel[pending[pi]]]
+                jid = srv.submit(jb["starts"], jb["l"], jb["p"], jb["q"], jb["seed"])
+                sub_t[jid] = t_start + (0.0 if arrivals is None else arrivals[pending[pi]])
+                pi += 1
+            srv.step()
+            for jid in srv.poll():
+                lat.append(time.perf_counter() - sub_t[jid])
+                counted.add_((srv.rows(jid) >= 0).sum())
+                srv.release(jid)
+                done += 1
+            if pi < len(pending) and arrivals is not None:
+                time.sleep(0.0002)
+        torch.cuda.synchronize(dev)
+        return time.perf_counter() - t_start, lat, int(counted.item())
+
+    # capacity: a batch of jobs submitted at once, back to back
+    cap_sel = list(range(min(len(jobs), 300)))
+    run_batch(cap_sel[:20])  # warm-up
+    span, _, steps = run_batch(cap_sel)
+    capacity = steps / span                                # steps/s
+    mean_steps = steps / len(cap_sel)                      # steps per job (this mix)
+    rate = args.load * capacity / mean_steps               # jobs/s
+    rng = np.random.default_rng(11)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=len(jobs)))
+    clocks = ClockSampler(local)
+    ticks0 = srv.stats()["ticks"]
+    clocks.start()
+    span, lat, steps = run_batch(list(range(len(jobs))), arrivals)
+    clk = clocks.stop()
+    ticks = srv.stats()["ticks"] - ticks0
+    st = n2v.n2v_stream_status(graph.handle, stream)
+    if st != n2v.N2V_OK:
+        raise RuntimeError(n2v.n2v_strerror(st))
+    # the jobs one at a time through the plain sampler (a bounded subset)
+    seq_sel = list(range(min(len(jobs), 40)))
+    seq_steps, seq_ms, seq_lat = 0, 0.0, []
+    for i in seq_sel:
+        jb = jobs[i]
+        s_d = torch.from_numpy(jb["starts"]).to(dev)
+        out = torch.empty((jb["size"], jb["l"]), dtype=torch.int32, device=dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        n2v.n2v_walk(graph.handle, s_d, jb["size"], 1, jb["l"], jb["p"], jb["q"], jb["seed"], 0, jb["size"], out, None,
+                     n2v.N2V_PLAIN, stream)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        seq_ms += a.elapsed_time(b)
+        seq_lat.append(a.elapsed_time(b) / 1e3)
+        seq_steps += int((out >= 0).sum())
+    srv.close()
+    lat = np.array(lat)
+    line = {
+        "metric": METRIC, "value": steps / span, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1,
+        "ms_per_step": span * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u64", "data": "synthetic",
+        "config": {"workload": wl.name, "desc": "serving on R-MAT scale 24, ef 16", "n": g.n, "nnz": g.nnz,
+                   "jobs": len(jobs), "job_size": "log-uniform in [1, 2^20] uniform starts, with replacement",
+                   "l": [10, 20, 40, 80], "pq": "log-uniform [0.25, 4], Q16", "arrivals": "Poisson",
+                   "load": args.load, "arena_bytes": arena_bytes, "tick_walkers": cfg.tick_walkers,
+                   "tune": best.as_dict(), "gen_s": round(gen_s, 2)},
+        "serving": {"throughput_steps_per_s": steps / span, "jobs_per_s": len(jobs) / span,
+                    "capacity_steps_per_s": capacity, "arrival_rate_jobs_per_s": rate,
+                    "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
+                    "latency_mean_s": float(lat.mean()), "makespan_s": span, "real_transitions": steps,
+                    "latency_to": "rows resident in HBM (job polled complete)"},
+        "sequential_plain": {"jobs": len(seq_sel), "value": seq_steps / (seq_ms / 1e3), "unit": UNIT,
+                             "service_time_p50_s": float(np.percentile(seq_lat, 50)),
+                             "note": "the first jobs one at a time through the plain sampler, no queueing"},
+        "gpu_launches": int(ticks),
+        "clocks": clk,
+    }
+    line["speedup_over_sequential_plain"] = line["value"] / line["sequential_plain"]["value"]
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "rmat24serve":
+        run_serving(args)
     else:
         run_ours(args)
 
