@@ -311,11 +311,11 @@ def run_ours(args):
     info = graph.info()
     l = wl.l
     n_start = g.n
-    W = n_start * r                       # walks per rank
+    from paper_1805_00280_gb300 import shard
+
+    r_total, walk_begin, W = shard.weak_shard(world, rank, n_start, r)  # rank k runs rounds [k r, (k+1) r)
     if args.walk_count:
         W = min(W, args.walk_count)
-    r_total = r * world                   # rank k runs rounds [k r, (k+1) r)
-    walk_begin = rank * W
     starts = torch.arange(n_start, dtype=torch.int32, device=dev)
     outs = [torch.empty((W, l), dtype=torch.int32, device=dev) for _ in pq]
     variant = n2v.VARIANTS[args.variant] | (n2v.N2V_FLAG_CUDA_GRAPH if cuda_graph else 0)
