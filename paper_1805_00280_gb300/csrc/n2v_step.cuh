@@ -238,27 +238,42 @@ __device__ __forceinline__ void gen_specials(const StepCtx& c, int mode, int32_t
                                              uint32_t a_p, uint32_t a_q, int lane) {
   const GraphView& g = *c.g;
   if (mode == 0) {
-    int32_t x_next = lane < c.dv ? __ldg(c.nv + lane) : 0;
-    for (int c0 = 0; c0 < c.dv; c0 += 32) {
-      const int i = c0 + lane;
-      int32_t pos = -1;
-      uint32_t cls = 0;
-      const int32_t x = x_next;
-      if (i + 32 < c.dv) x_next = __ldg(c.nv + i + 32);
-      if (i < c.dv) {
-        bool sp;
-        if (x == c.t32) sp = true;
-        else if (hub >= 0) sp = hub_find(g, hub, x) >= 0;
-        else {
-          const int p = lower_bound32(c.nt, c.dt, x);
-          sp = p < c.dt && __ldg(c.nt + p) == x;
+    // two candidates per lane and chunk: two independent searches in flight
+    auto member = [&](int32_t x) -> bool {
+      if (x == c.t32) return true;
+      if (hub >= 0) return hub_find(g, hub, x) >= 0;
+      const int p = lower_bound32(c.nt, c.dt, x);
+      return p < c.dt && __ldg(c.nt + p) == x;
+    };
+    for (int c0 = 0; c0 < c.dv; c0 += 64) {
+      const int i0 = c0 + lane, i1 = c0 + 32 + lane;
+      const int32_t x0 = i0 < c.dv ? __ldg(c.nv + i0) : -1;
+      const int32_t x1 = i1 < c.dv ? __ldg(c.nv + i1) : -1;
+      bool sp0 = false, sp1 = false;
+      if (hub < 0) {
+        // interleaved lower bounds over N(t)
+        int lo0 = 0, n0 = c.dt, lo1 = 0, n1 = c.dt;
+        while (n0 > 0 || n1 > 0) {
+          const int h0 = n0 >> 1, h1 = n1 >> 1;
+          const bool a0 = n0 > 0 && __ldg(c.nt + lo0 + h0) < x0;
+          const bool a1 = n1 > 0 && __ldg(c.nt + lo1 + h1) < x1;
+          if (n0 > 0) {
+            lo0 = a0 ? lo0 + h0 + 1 : lo0;
+            n0 = a0 ? n0 - h0 - 1 : h0;
+          }
+          if (n1 > 0) {
+            lo1 = a1 ? lo1 + h1 + 1 : lo1;
+            n1 = a1 ? n1 - h1 - 1 : h1;
+          }
         }
-        if (sp) {
-          pos = i;
-          cls = x == c.t32 ? 2u : 1u;
-        }
+        sp0 = i0 < c.dv && (x0 == c.t32 || (lo0 < c.dt && __ldg(c.nt + lo0) == x0));
+        sp1 = i1 < c.dv && (x1 == c.t32 || (lo1 < c.dt && __ldg(c.nt + lo1) == x1));
+      } else {
+        sp0 = i0 < c.dv && member(x0);
+        sp1 = i1 < c.dv && member(x1);
       }
-      sink_emit(k, sm, g, c.bv, pos, cls, a_p, a_q, lane);
+      sink_emit(k, sm, g, c.bv, sp0 ? i0 : -1, sp0 ? (x0 == c.t32 ? 2u : 1u) : 0u, a_p, a_q, lane);
+      if (c0 + 32 < c.dv) sink_emit(k, sm, g, c.bv, sp1 ? i1 : -1, sp1 ? (x1 == c.t32 ? 2u : 1u) : 0u, a_p, a_q, lane);
     }
     return;
   }
@@ -296,51 +311,75 @@ __device__ __forceinline__ void gen_specials(const StepCtx& c, int mode, int32_t
   const int ahead = min(sm.nbuf, nwin);
   for (int q = 0; q < ahead; ++q) stage_issue(sm, g, L, llen, q, lane);
   int wi = 0;
-  int32_t key_next = lane < nkeys ? (stage_v ? s_at(c, lane) : __ldg(c.nv + lane)) : 0;
+  // two keys per lane and chunk (keys kc + lane and kc + 32 + lane): two
+  // independent search chains in flight per lane
+  auto key_at = [&](int i) -> int32_t { return i < nkeys ? (stage_v ? s_at(c, i) : __ldg(c.nv + i)) : 0; };
+  int32_t next0 = key_at(lane), next1 = key_at(32 + lane);
   stage_wait(sm, 0);
-  for (int kc = 0; kc < nkeys; kc += 32) {
-    const int i = kc + lane;
-    const bool valid = i < nkeys;
-    const int32_t key = key_next;
-    if (i + 32 < nkeys) key_next = stage_v ? s_at(c, i + 32) : __ldg(c.nv + i + 32);  // next chunk, in flight
+  for (int kc = 0; kc < nkeys; kc += 64) {
+    const int i0 = kc + lane, i1 = kc + 32 + lane;
+    const int32_t key0 = next0, key1 = next1;
+    next0 = key_at(i0 + 64);  // the next chunk's keys, in flight
+    next1 = key_at(i1 + 64);
     // an element of N(v) equal to t is special whatever N(t) holds
-    const bool is_t = valid && !stage_v && key == c.t32;
-    bool pending = valid && !is_t;
-    int at = -1;  // index of key inside L, or -1
+    const bool is_t0 = i0 < nkeys && !stage_v && key0 == c.t32;
+    const bool is_t1 = i1 < nkeys && !stage_v && key1 == c.t32;
+    bool pend0 = i0 < nkeys && !is_t0, pend1 = i1 < nkeys && !is_t1;
+    int at0 = -1, at1 = -1;  // index of the key inside L, or -1
     for (;;) {
       const int b = wi & (sm.nbuf - 1);
       const int32_t* w = sm.win + b * (sm.wlen + 8) + stage_off(sm, L, wi);
       const int cnt = min(W, llen - wi * W);
       const bool last = wi == nwin - 1;
-      if (pending && (last || key <= w[cnt - 1])) {
-        // fixed-depth search over the power-of-two window (slots >= cnt read as +inf)
-        int lo = 0;
-        for (int s = W >> 1; s > 0; s >>= 1) {
-          const int probe = lo + s - 1;
-          lo += (probe < cnt && w[probe] < key) ? s : 0;
+      const int32_t wlast = w[cnt - 1];
+      const bool go0 = pend0 && (last || key0 <= wlast);
+      const bool go1 = pend1 && (last || key1 <= wlast);
+      if (go0 || go1) {
+        // fixed-depth searches over the power-of-two window (slots >= cnt read as +inf)
+        int lo0 = 0, lo1 = 0;
+        for (int st = W >> 1; st > 0; st >>= 1) {
+          const int p0 = lo0 + st - 1, p1 = lo1 + st - 1;
+          const int32_t v0 = p0 < cnt ? w[p0] : INT32_MAX;
+          const int32_t v1 = p1 < cnt ? w[p1] : INT32_MAX;
+          lo0 += v0 < key0 ? st : 0;
+          lo1 += v1 < key1 ? st : 0;
         }
-        if (lo < cnt && w[lo] < key) ++lo;
-        if (lo < cnt && w[lo] == key) at = wi * W + lo;
-        pending = false;
+        if (lo0 < cnt && w[lo0] < key0) ++lo0;
+        if (lo1 < cnt && w[lo1] < key1) ++lo1;
+        if (go0 && lo0 < cnt && w[lo0] == key0) at0 = wi * W + lo0;
+        if (go1 && lo1 < cnt && w[lo1] == key1) at1 = wi * W + lo1;
+        pend0 = pend0 && !go0;
+        pend1 = pend1 && !go1;
       }
-      if (!__any_sync(kFull, pending)) break;
+      if (!__any_sync(kFull, pend0 || pend1)) break;
       __syncwarp();
       if (wi + sm.nbuf < nwin) stage_issue(sm, g, L, llen, wi + sm.nbuf, lane);
       ++wi;
       stage_wait(sm, wi & (sm.nbuf - 1));
     }
-    int32_t pos = -1;
-    uint32_t cls = 0;
+    int32_t pos0 = -1, pos1 = -1;
+    uint32_t cls0 = 0, cls1 = 0;
     if (stage_v) {
-      if (at >= 0) {
-        pos = at;
-        cls = key == c.t32 ? 2u : 1u;
+      if (at0 >= 0) {
+        pos0 = at0;
+        cls0 = key0 == c.t32 ? 2u : 1u;
       }
-    } else if (is_t || at >= 0) {
-      pos = i;
-      cls = is_t ? 2u : 1u;
+      if (at1 >= 0) {
+        pos1 = at1;
+        cls1 = key1 == c.t32 ? 2u : 1u;
+      }
+    } else {
+      if (is_t0 || at0 >= 0) {
+        pos0 = i0;
+        cls0 = is_t0 ? 2u : 1u;
+      }
+      if (is_t1 || at1 >= 0) {
+        pos1 = i1;
+        cls1 = is_t1 ? 2u : 1u;
+      }
     }
-    sink_emit(k, sm, g, c.bv, pos, cls, a_p, a_q, lane);
+    sink_emit(k, sm, g, c.bv, pos0, cls0, a_p, a_q, lane);
+    if (kc + 32 < nkeys) sink_emit(k, sm, g, c.bv, pos1, cls1, a_p, a_q, lane);
   }
   // the windows after the current one may still be in flight
   for (int q = wi + 1; q < nwin && q <= wi + sm.nbuf - 1; ++q) stage_wait(sm, q & (sm.nbuf - 1));
