@@ -115,6 +115,7 @@ typedef struct n2v_graph_info {
   int64_t hub_min_degree; /* smallest degree among the hubs (0 if none) */
   int64_t hub_slots;      /* total slots of all hub hash sets */
   int64_t deg_hist[34];   /* [0]: degree 0; [i>=1]: degree in [2^(i-1), 2^i) */
+  uint32_t w_min, w_max;  /* extreme edge weights (1, 1 when unweighted) */
 } n2v_graph_info;
 
 /* Bytes of device memory the caller must provide as `aux` to n2v_graph_load
@@ -193,6 +194,20 @@ int n2v_walk(const n2v_graph* g, const int32_t* starts, int64_t n_starts, int32_
  * (walk_count / chunk_walkers), otherwise as n2v_walk.  Allocates nothing. */
 int n2v_walk_noalloc(const n2v_graph* g, const int32_t* starts, int64_t n_starts, int32_t r, int32_t l, double p,
                      double q, uint64_t seed, int64_t walk_begin, int64_t walk_count, int32_t* walks, void* stream);
+
+/* n2v_walk with FN-Approx (Section 3.4, Eq. 2-3): at a step from t to a
+ * popular v (deg v >= popular_degree) where t is not popular (deg t <
+ * popular_degree), the bounds LB, UB on the probability of moving to any
+ * x != t are computed from deg v, deg t, the Q16 return parameters and the
+ * graph's extreme weights; when UB - LB < eps the step samples by static
+ * weights w(v, x) with the same draw.  The decision is made in IEEE double,
+ * one rounding per operation in a fixed order, so every implementation of the
+ * rule takes the same branch.  The bounds assume t is a neighbour of v
+ * (undirected graphs).  The rows are approximate node2vec walks (not the exact
+ * distribution); eps = 0 gives the exact rows of n2v_walk. */
+int n2v_walk_approx(const n2v_graph* g, const int32_t* starts, int64_t n_starts, int32_t r, int32_t l, double p,
+                    double q, uint64_t seed, int64_t walk_begin, int64_t walk_count, int32_t* walks, void* ws,
+                    size_t ws_bytes, int variant, double eps, int64_t popular_degree, void* stream);
 
 /* Q16 return parameters exactly as n2v_walk rounds them (host function). */
 int n2v_alpha_q16(double p, double q, uint32_t* a_p, uint32_t* a_q);

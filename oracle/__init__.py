@@ -32,7 +32,8 @@ _lib = None
 
 def build(verbose: bool = False) -> str:
     """Compile liboracle.so with gcc (rebuilt when the sources or the host arch change)."""
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", SRC, "-o", LIB, "-lm"]
+    # no contraction of a*b+c: the FN-Approx decision is made in plain IEEE double
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", SRC, "-o", LIB, "-lm"]
     h = hashlib.sha256(" ".join(cmd).encode() + platform.machine().encode())
     for p in (SRC, HDR):
         with open(p, "rb") as f:
@@ -69,6 +70,11 @@ def lib() -> ctypes.CDLL:
         L.n2v_oracle_walk.restype = None
         L.n2v_oracle_traffic.argtypes = [vp, ctypes.c_int, vp, i64, vp, i64, vp, i32, vp]
         L.n2v_oracle_traffic.restype = None
+        L.n2v_oracle_approx_decide.argtypes = [i64, i64, u32, u32, u32, u32, ctypes.c_double, vp]
+        L.n2v_oracle_approx_decide.restype = ctypes.c_int
+        L.n2v_oracle_walk_approx.argtypes = [vp, vp, vp, vp, i64, i32, u32, u32, u64, vp, i64, ctypes.c_double,
+                                             i64, u32, u32, vp, vp]
+        L.n2v_oracle_walk_approx.restype = None
         _lib = L
     return _lib
 
@@ -152,3 +158,37 @@ def traffic(row_ptr, weighted: bool, starts, walk_ids, walks) -> tuple[int, int]
                              ids.ctypes.data, ids.shape[0], walks.ctypes.data, walks.shape[1],
                              out.ctypes.data)
     return int(out[0]), int(out[1])
+
+
+def approx_decide(deg_v: int, deg_t: int, a_p: int, a_q: int, w_min: int, w_max: int,
+                  eps: float) -> tuple[bool, float, float]:
+    """(approximate?, LB, UB) of FN-Approx for one step."""
+    b = np.zeros(2, dtype=np.float64)
+    d = lib().n2v_oracle_approx_decide(deg_v, deg_t, a_p, a_q, w_min, w_max, eps, b.ctypes.data)
+    return bool(d), float(b[0]), float(b[1])
+
+
+def walk_approx(row_ptr, col, w, starts, l: int, p: float, q: float, seed: int, walk_ids, eps: float,
+                popular: int, threads: int = 1) -> tuple[np.ndarray, int, int]:
+    """FN-Approx walks: (rows, approximated steps, 2nd-order steps).  w_min/w_max are the graph's."""
+    row_ptr, col, w = _csr(row_ptr, col, w)
+    starts = np.ascontiguousarray(starts, dtype=np.int32)
+    ids = np.ascontiguousarray(walk_ids, dtype=np.int64)
+    a_p, a_q = alpha_q16(p, q)
+    w_min = int(w.min()) if w is not None and w.size else 1
+    w_max = int(w.max()) if w is not None and w.size else 1
+    out = np.empty((ids.shape[0], l), dtype=np.int32)
+    counts = np.zeros((max(1, threads), 2), dtype=np.uint64)
+    L = lib()
+
+    def run(k: int, lo: int, hi: int) -> None:
+        L.n2v_oracle_walk_approx(row_ptr.ctypes.data, col.ctypes.data, _ptr(w), starts.ctypes.data, starts.shape[0],
+                                 l, a_p, a_q, seed, ids[lo:].ctypes.data, hi - lo, eps, popular, w_min, w_max,
+                                 out[lo:].ctypes.data, counts[k].ctypes.data)
+
+    if ids.shape[0]:
+        bounds = np.linspace(0, ids.shape[0], max(1, threads) + 1).astype(int)
+        with ThreadPoolExecutor(max_workers=max(1, threads)) as ex:
+            list(ex.map(lambda k: run(k, bounds[k], bounds[k + 1]), range(max(1, threads))))
+    tot = counts.sum(axis=0)
+    return out, int(tot[0]), int(tot[1])

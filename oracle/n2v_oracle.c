@@ -174,3 +174,73 @@ void n2v_oracle_traffic(const int64_t* row_ptr, int weighted, const int32_t* sta
   out[0] = steps;
   out[1] = bytes;
 }
+
+/* ---------------------------------------------------------------------- */
+/* FN-Approx (Section 3.4, Eq. 2-3).                                        */
+/* The bounds are those of the paper for 1/p <= 1 <= 1/q, written for any   */
+/* order of 1 and 1/q: a neighbour x != t has alpha 1 (common neighbour) or  */
+/* 1/q, at most min(deg t, deg v - 1) neighbours can be common, t itself     */
+/* carries 1/p, and every weight lies in [w_min, w_max].                     */
+
+int n2v_oracle_approx_decide(int64_t deg_v, int64_t deg_t, uint32_t a_p, uint32_t a_q, uint32_t w_min,
+                             uint32_t w_max, double eps, double bounds[2]) {
+  const double ip = (double)a_p / 65536.0; /* 1/p in Q16, exact in double */
+  const double iq = (double)a_q / 65536.0; /* 1/q */
+  const double wmin = (double)w_min, wmax = (double)w_max;
+  const double others = (double)(deg_v - 1);
+  const double cmax = (double)(deg_t < deg_v - 1 ? deg_t : deg_v - 1);
+  /* numerator of P(v -> x), x != t */
+  const double num_min = wmin * (iq < 1.0 ? iq : 1.0);
+  const double num_max = wmax * (iq < 1.0 ? 1.0 : iq);
+  /* the total over N(v) is smallest with the smaller alpha on as many
+   * neighbours as allowed, largest with the larger one */
+  const double all_q = ip + others * iq;                 /* no common neighbour */
+  const double most_1 = (ip + cmax) + (others - cmax) * iq; /* as many as allowed */
+  const double den_min = wmin * (iq >= 1.0 ? most_1 : all_q);
+  const double den_max = wmax * (iq >= 1.0 ? all_q : most_1);
+  const double lb = num_min / den_max;
+  const double ub = num_max / den_min;
+  if (bounds) {
+    bounds[0] = lb;
+    bounds[1] = ub;
+  }
+  return (ub - lb) < eps;
+}
+
+void n2v_oracle_walk_approx(const int64_t* row_ptr, const int32_t* col, const uint32_t* w,
+                            const int32_t* starts, int64_t n_starts, int32_t l, uint32_t a_p, uint32_t a_q,
+                            uint64_t seed, const int64_t* walk_ids, int64_t n_ids, double eps,
+                            int64_t popular, uint32_t w_min, uint32_t w_max, int32_t* out, uint64_t counts[2]) {
+  uint64_t n_approx = 0, n_second = 0;
+  for (int64_t i = 0; i < n_ids; ++i) {
+    uint64_t wid = (uint64_t)walk_ids[i];
+    int32_t* row = out + i * (int64_t)l;
+    int64_t t = -1;
+    int64_t v = starts[wid % (uint64_t)n_starts];
+    int32_t k = 0;
+    for (; k < l; ++k) {
+      uint64_t u = n2v_oracle_draw(seed, wid, (uint32_t)k);
+      int32_t kk = k; /* the step index the weights use: 0 means static weights */
+      if (k >= 1) {
+        int64_t dv = row_ptr[v + 1] - row_ptr[v], dt = row_ptr[t + 1] - row_ptr[t];
+        ++n_second;
+        if (dv >= popular && dt < popular &&
+            n2v_oracle_approx_decide(dv, dt, a_p, a_q, w_min, w_max, eps, NULL)) {
+          kk = 0;
+          ++n_approx;
+        }
+      }
+      int64_t j = n2v_oracle_step(row_ptr, col, w, t, v, kk, a_p, a_q, u, NULL);
+      if (j < 0) break;
+      int32_t x = col[row_ptr[v] + j];
+      row[k] = x;
+      t = v;
+      v = x;
+    }
+    for (; k < l; ++k) row[k] = -1;
+  }
+  if (counts) {
+    counts[0] = n_approx;
+    counts[1] = n_second;
+  }
+}

@@ -53,6 +53,25 @@ void n2v_oracle_walk(const int64_t* row_ptr, const int32_t* col, const uint32_t*
                      const int32_t* starts, int64_t n_starts, int32_t l, uint32_t a_p, uint32_t a_q,
                      uint64_t seed, const int64_t* walk_ids, int64_t n_ids, int32_t* out);
 
+/* FN-Approx (Section 3.4, Eq. 2-3): at a popular v (degree >= popular) reached
+ * from an unpopular t (degree < popular), the bounds
+ *   LB = num_min / den_max,  UB = num_max / den_min
+ * on the probability of moving to any x != t are computed from deg(v), deg(t),
+ * the Q16 return parameters and the extreme edge weights w_min, w_max of the
+ * graph; when UB - LB < eps the step ignores the 2nd-order factor and samples
+ * by static weights with the same draw.  The bounds and the comparison are
+ * evaluated in IEEE double, one rounding per operation, in the order written
+ * in n2v_oracle.c.  Returns 1 when the step is approximated. */
+int n2v_oracle_approx_decide(int64_t deg_v, int64_t deg_t, uint32_t a_p, uint32_t a_q, uint32_t w_min,
+                             uint32_t w_max, double eps, double bounds[2]);
+
+/* n2v_oracle_walk with FN-Approx applied at the steps where it decides so.
+ * counts (may be NULL) receives [approximated steps, all 2nd-order steps]. */
+void n2v_oracle_walk_approx(const int64_t* row_ptr, const int32_t* col, const uint32_t* w,
+                            const int32_t* starts, int64_t n_starts, int32_t l, uint32_t a_p, uint32_t a_q,
+                            uint64_t seed, const int64_t* walk_ids, int64_t n_ids, double eps,
+                            int64_t popular, uint32_t w_min, uint32_t w_max, int32_t* out, uint64_t counts[2]);
+
 /* Counts of the given walk rows: out[0] = real transitions (entries != -1),
  * out[1] = adjacency bytes by the per-step model
  *   16 + 4*deg(v)*(1 + weighted) + [k >= 1] * (16 + 4*deg(t)) + 4. */

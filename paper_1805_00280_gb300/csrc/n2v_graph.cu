@@ -76,6 +76,8 @@ __global__ void k_validate_stats(const int64_t* __restrict__ rp, const int32_t* 
       if (w) {
         sum += w[j];
         wpre[j] = sum;
+        atomicMax(&sc[kScWMax], (unsigned long long)w[j]);
+        atomicMax(&sc[kScWMin], (unsigned long long)(0xffffffffu - w[j]));  // max of complements = min
       }
     }
     if (!w) sum = (uint64_t)d;
@@ -317,6 +319,8 @@ int n2v_graph_load(const int64_t* row_ptr, const int32_t* col, const uint32_t* w
     g->info.weighted = weighted;
     g->info.max_degree = (int64_t)sc[kScMaxDeg];
     g->info.max_wsum = (uint64_t)sc[kScMaxWsum];
+    g->info.w_min = weighted && nnz > 0 ? 0xffffffffu - (uint32_t)sc[kScWMin] : 1u;
+    g->info.w_max = weighted && nnz > 0 ? (uint32_t)sc[kScWMax] : 1u;
     for (int i = 0; i < 34; ++i) g->info.deg_hist[i] = (int64_t)sc[kScHist + i];
     rc = build_hubs(g, L, s);
   }

@@ -45,6 +45,11 @@ struct WalkJob {
   uint64_t seed;
   int32_t* walks;      // [count][l]
   uint32_t* status;
+  // FN-Approx (Section 3.4): off when approx == 0
+  int approx;
+  double approx_eps;
+  int64_t approx_popular;  // popular: degree >= this
+  uint32_t w_min, w_max;   // extreme edge weights of the graph
 };
 
 // Tuning resolved for a launch.
@@ -255,8 +260,34 @@ enum : int {
   kScHubCount = 3,
   kScSlotCount = 4,
   kScHist = 8,  // 34 words
+  kScWMin = 42,
+  kScWMax = 43,
   kScWords = 64
 };
+
+// FN-Approx decision (Section 3.4, Eq. 2-3) for a step at v (degree dv)
+// reached from t (degree dt): bounds on the probability of any x != t,
+// evaluated in IEEE double with one rounding per operation in a fixed order
+// (the _rn intrinsics forbid contraction), so that every implementation of
+// the same formula takes the same branch.  The bounds assume t is a
+// neighbour of v (undirected graphs).
+__device__ __forceinline__ bool approx_decide(int64_t dv, int64_t dt, uint32_t a_p, uint32_t a_q, uint32_t w_min,
+                                              uint32_t w_max, double eps) {
+  const double ip = __ddiv_rn((double)a_p, 65536.0);
+  const double iq = __ddiv_rn((double)a_q, 65536.0);
+  const double wmin = (double)w_min, wmax = (double)w_max;
+  const double others = (double)(dv - 1);
+  const double cmax = (double)(dt < dv - 1 ? dt : dv - 1);
+  const double num_min = __dmul_rn(wmin, iq < 1.0 ? iq : 1.0);
+  const double num_max = __dmul_rn(wmax, iq < 1.0 ? 1.0 : iq);
+  const double all_q = __dadd_rn(ip, __dmul_rn(others, iq));
+  const double most_1 = __dadd_rn(__dadd_rn(ip, cmax), __dmul_rn(__dsub_rn(others, cmax), iq));
+  const double den_min = __dmul_rn(wmin, iq >= 1.0 ? most_1 : all_q);
+  const double den_max = __dmul_rn(wmax, iq >= 1.0 ? all_q : most_1);
+  const double lb = __ddiv_rn(num_min, den_max);
+  const double ub = __ddiv_rn(num_max, den_min);
+  return __dsub_rn(ub, lb) < eps;
+}
 
 // n2v_walk.cu
 LaunchCfg resolve_launch(const n2v_graph* g, int variant);

@@ -78,8 +78,12 @@ __global__ void __launch_bounds__(256, 3) k_serve(GraphView g, const DevSlice* _
           for (int kk = k; kk < S.l; ++kk) row[kk] = -1;
         break;
       }
-      const int32_t x = warp_binned_step(g, alive, t, v, k, (uint64_t)wid, S.seed, S.a_p, S.a_q, L.thread_max_deg, sm,
-                                         L.stream_ratio, lane);
+      WalkJob J;  // the slice's parameters (serving is exact: no FN-Approx)
+      J.seed = S.seed;
+      J.a_p = S.a_p;
+      J.a_q = S.a_q;
+      J.approx = 0;
+      const int32_t x = warp_binned_step(g, alive, t, v, k, (uint64_t)wid, J, L.thread_max_deg, sm, L.stream_ratio, lane);
       if (mine) row[k] = alive ? x : -1;
       if (alive) {
         if (x < 0) {

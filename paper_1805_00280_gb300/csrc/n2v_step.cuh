@@ -558,12 +558,43 @@ __device__ __forceinline__ int32_t warp_step(const GraphView& g, int64_t t, int6
 }
 
 // ---------------------------------------------------------------------------
+// One lane, static weights only (superstep 0 of Algorithm 1, and the steps
+// FN-Approx approximates): first j with W_j > floor(u * W_last / 2^64).
+__device__ __forceinline__ int32_t static_step(const GraphView& g, int64_t bv, int64_t ev, uint64_t u) {
+  const int64_t dv = ev - bv;
+  if (dv <= 0) return -1;
+  if (!g.w) return __ldg(g.col + bv + (int64_t)scale_draw(u, (uint64_t)dv));
+  const uint64_t T = __ldg(g.wpre + ev - 1);
+  if (T == 0) return -1;
+  const uint64_t r = scale_draw(u, T);
+  int64_t lo = 0, n = dv;  // first index with wpre > r
+  while (n > 0) {
+    const int64_t half = n >> 1;
+    if (__ldg(g.wpre + bv + lo + half) <= r) {
+      lo += half + 1;
+      n -= half + 1;
+    } else {
+      n = half;
+    }
+  }
+  return __ldg(g.col + bv + lo);
+}
+
+// Does FN-Approx replace this 2nd-order step by a static-weight one?
+__device__ __forceinline__ bool approx_here(const WalkJob& J, int k, int64_t dv, int64_t dt) {
+  return J.approx && k > 0 && dv >= J.approx_popular && dt < J.approx_popular &&
+         approx_decide(dv, dt, J.a_p, J.a_q, J.w_min, J.w_max, J.approx_eps);
+}
+
+// ---------------------------------------------------------------------------
 // One step for the 32 walkers a warp owns (one per lane).  Steps whose
 // degrees are all <= thr run on their own lane (thread bin); the others are
 // taken one after another by the whole warp (warp bin).
 __device__ __forceinline__ int32_t warp_binned_step(const GraphView& g, bool alive, int64_t t, int64_t v, int k,
-                                                    uint64_t wid, uint64_t seed, uint32_t a_p, uint32_t a_q,
-                                                    int thr, WarpSmem& sm, int stream_ratio, int lane) {
+                                                    uint64_t wid, const WalkJob& J, int thr, WarpSmem& sm,
+                                                    int stream_ratio, int lane) {
+  const uint64_t seed = J.seed;
+  const uint32_t a_p = J.a_p, a_q = J.a_q;
   int32_t x = -1;
   bool small = false;
   uint64_t u = 0;
@@ -577,8 +608,13 @@ __device__ __forceinline__ int32_t warp_binned_step(const GraphView& g, bool ali
       et = g.rp[t + 1];
     }
     u = philox_draw(seed, wid, (uint32_t)k);
-    small = ev - bv <= thr && (k == 0 || et - bt <= thr);
-    if (small) x = thread_step(g, t, v, k, u, a_p, a_q);
+    if (approx_here(J, k, ev - bv, et - bt)) {
+      small = true;  // taken on this lane, by static weights
+      x = static_step(g, bv, ev, u);
+    } else {
+      small = ev - bv <= thr && (k == 0 || et - bt <= thr);
+      if (small) x = thread_step(g, t, v, k, u, a_p, a_q);
+    }
   }
   unsigned wm = __ballot_sync(kFull, alive && !small);
   while (wm) {

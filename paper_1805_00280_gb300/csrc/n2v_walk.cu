@@ -39,7 +39,15 @@ __global__ void __launch_bounds__(256) k_plain_step(GraphView g, WalkJob J, int 
     }
     t = (k == 1) ? s0 : row[k - 2];
   }
-  row[k] = thread_step(g, t, v, k, philox_draw(J.seed, (uint64_t)wid, (uint32_t)k), J.a_p, J.a_q);
+  const uint64_t u = philox_draw(J.seed, (uint64_t)wid, (uint32_t)k);
+  if (J.approx && k > 0) {
+    const int64_t bv = g.rp[v], ev = g.rp[v + 1];
+    if (approx_here(J, k, ev - bv, g.rp[t + 1] - g.rp[t])) {
+      row[k] = static_step(g, bv, ev, u);
+      return;
+    }
+  }
+  row[k] = thread_step(g, t, v, k, u, J.a_p, J.a_q);
 }
 
 // ---------------------------------------------------------------------------
@@ -73,8 +81,7 @@ __global__ void __launch_bounds__(256) k_binned_step(GraphView g, WalkJob J, int
       atomicOr(J.status, kStInvalidArg);
     }
   }
-  const int32_t x = warp_binned_step(g, alive, t, v, k, (uint64_t)wid, J.seed, J.a_p, J.a_q, L.thread_max_deg, sm,
-                                     L.stream_ratio, lane);
+  const int32_t x = warp_binned_step(g, alive, t, v, k, (uint64_t)wid, J, L.thread_max_deg, sm, L.stream_ratio, lane);
   if (mine) row[k] = alive ? x : -1;
   if (sm.timed_out && lane == 0) atomicOr(J.status, kStTimeout);
 }
@@ -120,8 +127,8 @@ __global__ void __launch_bounds__(256, MINB) k_persistent(GraphView g, WalkJob J
           for (int kk = k; kk < J.l; ++kk) row[kk] = -1;
         break;
       }
-      const int32_t x = warp_binned_step(g, alive, t, v, k, (uint64_t)wid, J.seed, J.a_p, J.a_q, L.thread_max_deg, sm,
-                                         L.stream_ratio, lane);
+      const int32_t x = warp_binned_step(g, alive, t, v, k, (uint64_t)wid, J, L.thread_max_deg, sm, L.stream_ratio,
+                                         lane);
       if (mine) row[k] = alive ? x : -1;
       if (alive) {
         if (x < 0) {
@@ -235,6 +242,9 @@ struct WalkCall {
   int32_t* walks;
   void* ws;
   int variant;
+  int approx;  // FN-Approx parameters (approx == 0: exact walks)
+  double approx_eps;
+  int64_t approx_popular;
 };
 
 // Enqueue the launches of one call on stream s.
@@ -250,6 +260,11 @@ static cudaError_t issue(const n2v_graph* g, const WalkCall& c, cudaStream_t s) 
   J.seed = c.seed;
   J.walks = c.walks;
   J.status = g->status;
+  J.approx = c.approx;
+  J.approx_eps = c.approx_eps;
+  J.approx_popular = c.approx_popular;
+  J.w_min = g->info.w_min;
+  J.w_max = g->info.w_max;
   const int base = c.variant & 0xff;
   if (base == N2V_PLAIN) {
     const unsigned blocks = (unsigned)((c.count + 255) / 256);
@@ -368,9 +383,28 @@ int n2v_walk_ws_bytes(const n2v_graph* g, int64_t walk_count, int32_t l, int var
   return N2V_OK;
 }
 
+static int walk_impl(const n2v_graph* g, const int32_t* starts, int64_t n_starts, int32_t r, int32_t l, double p,
+                     double q, uint64_t seed, int64_t walk_begin, int64_t walk_count, int32_t* walks, void* ws,
+                     size_t ws_bytes, int variant, int approx, double eps, int64_t popular, void* stream);
+
 int n2v_walk(const n2v_graph* g, const int32_t* starts, int64_t n_starts, int32_t r, int32_t l, double p, double q,
              uint64_t seed, int64_t walk_begin, int64_t walk_count, int32_t* walks, void* ws, size_t ws_bytes,
              int variant, void* stream) {
+  return walk_impl(g, starts, n_starts, r, l, p, q, seed, walk_begin, walk_count, walks, ws, ws_bytes, variant, 0, 0.0,
+                   0, stream);
+}
+
+int n2v_walk_approx(const n2v_graph* g, const int32_t* starts, int64_t n_starts, int32_t r, int32_t l, double p,
+                    double q, uint64_t seed, int64_t walk_begin, int64_t walk_count, int32_t* walks, void* ws,
+                    size_t ws_bytes, int variant, double eps, int64_t popular_degree, void* stream) {
+  if (!(eps >= 0.0) || !isfinite(eps) || popular_degree < 1) return N2V_ERR_INVALID_ARG;
+  return walk_impl(g, starts, n_starts, r, l, p, q, seed, walk_begin, walk_count, walks, ws, ws_bytes, variant, 1, eps,
+                   popular_degree, stream);
+}
+
+static int walk_impl(const n2v_graph* g, const int32_t* starts, int64_t n_starts, int32_t r, int32_t l, double p,
+                     double q, uint64_t seed, int64_t walk_begin, int64_t walk_count, int32_t* walks, void* ws,
+                     size_t ws_bytes, int variant, int approx, double eps, int64_t popular, void* stream) {
   if (!g || l < 1 || r < 1 || n_starts < 1 || walk_begin < 0 || walk_count < 0) return N2V_ERR_INVALID_ARG;
   const int base = variant & 0xff;
   if (base != N2V_PLAIN && base != N2V_BINNED && base != N2V_PERSISTENT) return N2V_ERR_INVALID_ARG;
@@ -401,6 +435,9 @@ int n2v_walk(const n2v_graph* g, const int32_t* starts, int64_t n_starts, int32_
   c.walks = walks;
   c.ws = ws;
   c.variant = base;
+  c.approx = approx;
+  c.approx_eps = eps;
+  c.approx_popular = popular;
   cudaStream_t s = (cudaStream_t)stream;
   if (variant & N2V_FLAG_CUDA_GRAPH) return issue_graph(const_cast<n2v_graph*>(g), c, s);
   return issue(g, c, s) == cudaSuccess ? N2V_OK : N2V_ERR_CUDA;
@@ -543,6 +580,11 @@ extern "C" int n2v_walk_noalloc(const n2v_graph* g, const int32_t* starts, int64
   J.a_q = a_q;
   J.seed = seed;
   J.status = g->status;
+  J.approx = 0;
+  J.approx_eps = 0.0;
+  J.approx_popular = 0;
+  J.w_min = g->info.w_min;
+  J.w_max = g->info.w_max;
   const int64_t per = chunks == 1 ? walk_count : g->tune.chunk_walkers;
   for (int64_t ci = 0; ci < chunks; ++ci) {
     const int64_t lo = ci * per;

@@ -58,7 +58,7 @@ class n2v_graph_info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("weighted", ctypes.c_int32),
                 ("hub_count", ctypes.c_int32), ("max_degree", ctypes.c_int64), ("max_wsum", ctypes.c_uint64),
                 ("hub_min_degree", ctypes.c_int64), ("hub_slots", ctypes.c_int64),
-                ("deg_hist", ctypes.c_int64 * 34)]
+                ("deg_hist", ctypes.c_int64 * 34), ("w_min", ctypes.c_uint32), ("w_max", ctypes.c_uint32)]
 
 
 class n2v_job(ctypes.Structure):
@@ -105,6 +105,8 @@ def lib() -> ctypes.CDLL:
         L.n2v_walk.argtypes = [vp, vp, i64, i32, i32, dbl, dbl, u64, i64, i64, vp, vp, sz, ctypes.c_int, vp]
         L.n2v_walk_traffic.argtypes = [vp, vp, i64, i64, i64, i32, vp, vp, vp]
         L.n2v_walk_noalloc.argtypes = [vp, vp, i64, i32, i32, dbl, dbl, u64, i64, i64, vp, vp]
+        L.n2v_walk_approx.argtypes = [vp, vp, i64, i32, i32, dbl, dbl, u64, i64, i64, vp, vp, sz, ctypes.c_int, dbl,
+                                      i64, vp]
         L.n2v_stream_status.argtypes = [vp, vp]
         L.n2v_strerror.argtypes = [ctypes.c_int]
         L.n2v_strerror.restype = ctypes.c_char_p
@@ -209,6 +211,15 @@ def n2v_walk(handle: int, starts, n_starts: int, r: int, l: int, p: float, q: fl
     rc = lib().n2v_walk(handle, _ptr(starts), n_starts, r, l, p, q, seed, walk_begin, walk_count, _ptr(walks),
                         _ptr(ws), ws_bytes, variant, _stream(stream))
     _check(rc, "n2v_walk")
+
+
+def n2v_walk_approx(handle: int, starts, n_starts: int, r: int, l: int, p: float, q: float, seed: int,
+                    walk_begin: int, walk_count: int, walks, ws, variant: int, eps: float, popular: int,
+                    stream=None) -> None:
+    ws_bytes = 0 if ws is None else ws.numel() * ws.element_size()
+    rc = lib().n2v_walk_approx(handle, _ptr(starts), n_starts, r, l, p, q, seed, walk_begin, walk_count, _ptr(walks),
+                               _ptr(ws), ws_bytes, variant, eps, popular, _stream(stream))
+    _check(rc, "n2v_walk_approx")
 
 
 def n2v_walk_noalloc(handle: int, starts, n_starts: int, r: int, l: int, p: float, q: float, seed: int,
@@ -361,7 +372,7 @@ class Graph:
 
 def walk(graph: Graph, starts, r: int, l: int, p: float, q: float, seed: int, variant: str | int = "persistent",
          walk_begin: int = 0, walk_count: int | None = None, out=None, ws=None, stream=None,
-         cuda_graph: bool = False) -> torch.Tensor:
+         cuda_graph: bool = False, approx: tuple[float, int] | None = None) -> torch.Tensor:
     """Allocate (if needed) and fill int32 walks [walk_count, l] on the graph's device."""
     dev = graph.row_ptr.device
     starts = torch.as_tensor(starts, dtype=torch.int32).to(dev).contiguous()
@@ -376,7 +387,11 @@ def walk(graph: Graph, starts, r: int, l: int, p: float, q: float, seed: int, va
     need = n2v_walk_ws_bytes(graph.handle, walk_count, l, v)
     if need and (ws is None or ws.numel() * ws.element_size() < need):
         ws = torch.empty(need // 8 + 32, dtype=torch.int64, device=dev)
-    n2v_walk(graph.handle, starts, n_starts, r, l, p, q, seed, walk_begin, walk_count, out, ws, v, stream)
+    if approx is not None:
+        n2v_walk_approx(graph.handle, starts, n_starts, r, l, p, q, seed, walk_begin, walk_count, out, ws, v,
+                        float(approx[0]), int(approx[1]), stream)
+    else:
+        n2v_walk(graph.handle, starts, n_starts, r, l, p, q, seed, walk_begin, walk_count, out, ws, v, stream)
     return out
 
 
