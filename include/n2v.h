@@ -300,6 +300,13 @@ int n2v_serve_stats(n2v_server* s, n2v_serve_stats_t* st);
 /* Destroy the server (synchronise the stream first; the arena stays the caller's). */
 void n2v_serve_destroy(n2v_server* s);
 
+/* Failure-path self-test (SURVEY's failure detection, no paper counterpart):
+ * launch one warp that waits on an mbarrier nothing arrives on, with the
+ * samplers' bounded wait and a limit of limit_cycles SM cycles (1 .. 2^34).
+ * It gives up, records N2V_ERR_TIMEOUT in the status word of g and returns;
+ * no fault, no trap.  n2v_stream_status then reports (and clears) it. */
+int n2v_selftest_timeout(const n2v_graph* g, int64_t limit_cycles, void* stream);
+
 /* Static text for a status code. */
 const char* n2v_strerror(int code);
 

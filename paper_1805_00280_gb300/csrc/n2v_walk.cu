@@ -175,6 +175,21 @@ __global__ void k_traffic(const int64_t* __restrict__ rp, int weighted, const in
 }
 
 // ---------------------------------------------------------------------------
+// Self-test of the bounded waits: one warp waits on an mbarrier that nothing
+// arrives on, with the samplers' wait routine and a short limit, then records
+// the timeout in the status word and returns (no copy is in flight).
+__global__ void k_selftest_wait(uint32_t* status, long long limit) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
+  const bool ok = mbar_wait_bounded(&bar, 0u, limit);
+  if (!ok && threadIdx.x == 0) atomicOr(status, kStTimeout);
+}
+
+// ---------------------------------------------------------------------------
 // launch configuration
 
 static int smem_per_block(const LaunchCfg& c) { return (c.block_threads / 32) * warp_smem_bytes(c); }
@@ -453,6 +468,12 @@ int n2v_walk_traffic(const n2v_graph* g, const int32_t* starts, int64_t n_starts
   const unsigned blocks = (unsigned)std::min<int64_t>((walk_count + 255) / 256, (int64_t)g->sms * 16);
   k_traffic<<<blocks, 256, 0, s>>>(g->view.rp, g->weighted, starts, n_starts, walk_begin, walk_count, l, walks,
                                    (unsigned long long*)out2);
+  return cudaGetLastError() == cudaSuccess ? N2V_OK : N2V_ERR_CUDA;
+}
+
+int n2v_selftest_timeout(const n2v_graph* g, int64_t limit_cycles, void* stream) {
+  if (!g || limit_cycles < 1 || limit_cycles > (1ll << 34)) return N2V_ERR_INVALID_ARG;
+  k_selftest_wait<<<1, 32, 0, (cudaStream_t)stream>>>(g->status, (long long)limit_cycles);
   return cudaGetLastError() == cudaSuccess ? N2V_OK : N2V_ERR_CUDA;
 }
 

@@ -105,6 +105,7 @@ def lib() -> ctypes.CDLL:
         L.n2v_walk.argtypes = [vp, vp, i64, i32, i32, dbl, dbl, u64, i64, i64, vp, vp, sz, ctypes.c_int, vp]
         L.n2v_walk_traffic.argtypes = [vp, vp, i64, i64, i64, i32, vp, vp, vp]
         L.n2v_walk_noalloc.argtypes = [vp, vp, i64, i32, i32, dbl, dbl, u64, i64, i64, vp, vp]
+        L.n2v_selftest_timeout.argtypes = [vp, i64, vp]
         L.n2v_walk_approx.argtypes = [vp, vp, i64, i32, i32, dbl, dbl, u64, i64, i64, vp, vp, sz, ctypes.c_int, dbl,
                                       i64, vp]
         L.n2v_stream_status.argtypes = [vp, vp]
@@ -234,6 +235,10 @@ def n2v_walk_traffic(handle: int, starts, n_starts: int, walk_begin: int, walk_c
                      out2, stream=None) -> None:
     _check(lib().n2v_walk_traffic(handle, _ptr(starts), n_starts, walk_begin, walk_count, l, _ptr(walks),
                                   _ptr(out2), _stream(stream)), "n2v_walk_traffic")
+
+
+def n2v_selftest_timeout(handle: int, limit_cycles: int, stream=None) -> None:
+    _check(lib().n2v_selftest_timeout(handle, limit_cycles, _stream(stream)), "n2v_selftest_timeout")
 
 
 def n2v_stream_status(handle: int, stream=None) -> int:

@@ -276,3 +276,16 @@ def test_invalid_graph_is_rejected(bad):
     with pytest.raises(n2v.N2VError) as e:
         n2v.Graph(rp, col)
     assert e.value.code == n2v.N2V_ERR_INVALID_GRAPH
+
+
+def test_bounded_wait_times_out_cleanly():
+    """A wait that can never complete gives up after its limit, reports
+    N2V_ERR_TIMEOUT through the status word, and leaves the context usable."""
+    g = SMALL["und7"]
+    graph = n2v.Graph.from_csr(g)
+    n2v.n2v_selftest_timeout(graph.handle, 2_000_000)  # about 1 ms of SM clock
+    assert n2v.n2v_stream_status(graph.handle) == n2v.N2V_ERR_TIMEOUT
+    assert n2v.n2v_stream_status(graph.handle) == n2v.N2V_OK  # cleared
+    starts = np.arange(g.n, dtype=np.int32)
+    want = oracle_rows(g, starts, 5, 1.0, 1.0, 2, np.arange(g.n))
+    np.testing.assert_array_equal(gpu_rows(g, starts, 1, 5, 1.0, 1.0, 2, "persistent", graph=graph), want)
