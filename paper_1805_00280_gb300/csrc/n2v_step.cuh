@@ -314,8 +314,19 @@ __device__ __forceinline__ void gen_specials(const StepCtx& c, int mode, int32_t
   // two keys per lane and chunk (keys kc + lane and kc + 32 + lane): two
   // independent search chains in flight per lane
   auto key_at = [&](int i) -> int32_t { return i < nkeys ? (stage_v ? s_at(c, i) : __ldg(c.nv + i)) : 0; };
+  // after a window lands: a short (last) window is padded to wlen with +inf
+  // so that the fixed-depth search needs no bounds test
+  auto land = [&](int wj) {
+    stage_wait(sm, wj & (sm.nbuf - 1));
+    const int cnt = min(W, llen - wj * W);
+    if (cnt < W) {
+      int32_t* w = sm.win + (wj & (sm.nbuf - 1)) * (sm.wlen + 8) + stage_off(sm, L, wj);
+      for (int q = cnt + lane; q < W; q += 32) w[q] = INT32_MAX;
+      __syncwarp();
+    }
+  };
   int32_t next0 = key_at(lane), next1 = key_at(32 + lane);
-  stage_wait(sm, 0);
+  land(0);
   for (int kc = 0; kc < nkeys; kc += 64) {
     const int i0 = kc + lane, i1 = kc + 32 + lane;
     const int32_t key0 = next0, key1 = next1;
@@ -337,12 +348,9 @@ __device__ __forceinline__ void gen_specials(const StepCtx& c, int mode, int32_t
       if (go0 || go1) {
         // fixed-depth searches over the power-of-two window (slots >= cnt read as +inf)
         int lo0 = 0, lo1 = 0;
-        for (int st = W >> 1; st > 0; st >>= 1) {
-          const int p0 = lo0 + st - 1, p1 = lo1 + st - 1;
-          const int32_t v0 = p0 < cnt ? w[p0] : INT32_MAX;
-          const int32_t v1 = p1 < cnt ? w[p1] : INT32_MAX;
-          lo0 += v0 < key0 ? st : 0;
-          lo1 += v1 < key1 ? st : 0;
+        for (int st = W >> 1; st > 0; st >>= 1) {  // slots [cnt, W) hold +inf
+          lo0 += w[lo0 + st - 1] < key0 ? st : 0;
+          lo1 += w[lo1 + st - 1] < key1 ? st : 0;
         }
         if (lo0 < cnt && w[lo0] < key0) ++lo0;
         if (lo1 < cnt && w[lo1] < key1) ++lo1;
@@ -355,7 +363,7 @@ __device__ __forceinline__ void gen_specials(const StepCtx& c, int mode, int32_t
       __syncwarp();
       if (wi + sm.nbuf < nwin) stage_issue(sm, g, L, llen, wi + sm.nbuf, lane);
       ++wi;
-      stage_wait(sm, wi & (sm.nbuf - 1));
+      land(wi);
     }
     int32_t pos0 = -1, pos1 = -1;
     uint32_t cls0 = 0, cls1 = 0;
