@@ -162,6 +162,46 @@ __device__ __forceinline__ int stage_off(const WarpSmem& sm, const int32_t* L, i
   return (int)(((uintptr_t)(L + wi * sm.wlen) & 15) >> 2);
 }
 
+// 32-bit load from a shared-memory byte address.
+__device__ __forceinline__ int32_t lds32(uint32_t addr) {
+  int32_t v;
+  asm volatile("ld.shared.s32 %0, [%1];" : "=r"(v) : "r"(addr));
+  return v;
+}
+
+// Number of window slots below key0 and key1 in a sorted window of W slots
+// (W a power of two; slots past the data hold +inf) at shared address base:
+// two interleaved fixed-depth searches, fully unrolled.
+template <int W>
+__device__ __forceinline__ void window_rank2(uint32_t base, int32_t key0, int32_t key1, int& lo0, int& lo1) {
+  int a = 0, b = 0;
+#pragma unroll
+  for (int st = W >> 1; st > 0; st >>= 1) {
+    const int32_t v0 = lds32(base + 4u * (uint32_t)(a + st - 1));
+    const int32_t v1 = lds32(base + 4u * (uint32_t)(b + st - 1));
+    a += v0 < key0 ? st : 0;
+    b += v1 < key1 ? st : 0;
+  }
+  lo0 = a;
+  lo1 = b;
+}
+
+__device__ __forceinline__ void window_rank2_any(int W, uint32_t base, int32_t key0, int32_t key1, int& lo0, int& lo1) {
+  if (W == 1024) {
+    window_rank2<1024>(base, key0, key1, lo0, lo1);
+    return;
+  }
+  int a = 0, b = 0;  // other window sizes: the same search, not unrolled
+  for (int st = W >> 1; st > 0; st >>= 1) {
+    const int32_t v0 = lds32(base + 4u * (uint32_t)(a + st - 1));
+    const int32_t v1 = lds32(base + 4u * (uint32_t)(b + st - 1));
+    a += v0 < key0 ? st : 0;
+    b += v1 < key1 ? st : 0;
+  }
+  lo0 = a;
+  lo1 = b;
+}
+
 // Fill staging window wi of list L (length llen) into buffer wi % nbuf: the
 // 16-byte-aligned body by one TMA bulk copy, the ragged tail that would read
 // past the 16-byte-aligned end of col by plain loads.
@@ -216,7 +256,9 @@ __device__ __forceinline__ uint64_t special_delta(const GraphView& g, int64_t bv
 
 __device__ __forceinline__ void sink_emit(SpecialSink& k, WarpSmem& sm, const GraphView& g, int64_t bv, int32_t pos,
                                           uint32_t cls, uint32_t a_p, uint32_t a_q, int lane) {
-  k.dpart += special_delta(g, bv, pos, cls, a_p, a_q);
+  // unweighted: a special's correction depends only on its class, so the
+  // total comes from the class counts instead of a per-lane sum
+  if (g.w) k.dpart += special_delta(g, bv, pos, cls, a_p, a_q);
   const unsigned m = __ballot_sync(kFull, cls != 0u);
   const unsigned m2 = __ballot_sync(kFull, cls == 2u);
   if (m2) k.ord_t = k.cnt + __popc(m & ((1u << (__ffs(m2) - 1)) - 1u));
@@ -234,7 +276,7 @@ __device__ __forceinline__ void sink_emit(SpecialSink& k, WarpSmem& sm, const Gr
 // Enumerate the specials of the step in increasing position into `k`.
 // mode 0: probe over N(v) (membership in N(t)); 1: probe over S (position in
 // N(v)); 2: stage N(v), candidates S; 3: stage N(t), candidates N(v).
-__device__ __forceinline__ void gen_specials(const StepCtx& c, int mode, int32_t hub, WarpSmem& sm, SpecialSink& k,
+__device__ __forceinline__ void gen_specials(StepCtx& c, int mode, int32_t hub, WarpSmem& sm, SpecialSink& k,
                                              uint32_t a_p, uint32_t a_q, int lane) {
   const GraphView& g = *c.g;
   if (mode == 0) {
@@ -305,11 +347,16 @@ __device__ __forceinline__ void gen_specials(const StepCtx& c, int mode, int32_t
   const bool stage_v = mode == 2;
   const int32_t* L = stage_v ? c.nv : c.nt;
   const int llen = stage_v ? c.dv : c.dt;
-  const int nkeys = stage_v ? c.slen : c.dv;
   const int W = sm.wlen;
   const int nwin = (llen + W - 1) / W;
   const int ahead = min(sm.nbuf, nwin);
   for (int q = 0; q < ahead; ++q) stage_issue(sm, g, L, llen, q, lane);
+  if (stage_v && c.ins < 0) {  // t's slot in S = N(t) + {t}, searched while the copies fly
+    c.ins = lower_bound32(c.nt, c.dt, c.t32);
+    c.has_self = c.ins < c.dt && __ldg(c.nt + c.ins) == c.t32;
+    c.slen = c.dt + (c.has_self ? 0 : 1);
+  }
+  const int nkeys = stage_v ? c.slen : c.dv;
   int wi = 0;
   // two keys per lane and chunk (keys kc + lane and kc + 32 + lane): two
   // independent search chains in flight per lane
@@ -325,37 +372,45 @@ __device__ __forceinline__ void gen_specials(const StepCtx& c, int mode, int32_t
       __syncwarp();
     }
   };
+  // keys two chunks ahead are in flight while a chunk is searched
+  // the resident window: shared address, length, last element (+inf for the last window)
+  uint32_t wbase = 0;
+  int wcnt = 0;
+  int32_t wlast = 0;
+  bool wlast_inf = false;
+  auto set_window = [&](int wj) {
+    wbase = smem_addr(sm.win + (wj & (sm.nbuf - 1)) * (sm.wlen + 8) + stage_off(sm, L, wj));
+    wcnt = min(W, llen - wj * W);
+    wlast_inf = wj == nwin - 1;
+    wlast = lds32(wbase + 4u * (uint32_t)(wcnt - 1));
+  };
   int32_t next0 = key_at(lane), next1 = key_at(32 + lane);
+  int32_t after0 = key_at(64 + lane), after1 = key_at(96 + lane);
   land(0);
+  set_window(0);
   for (int kc = 0; kc < nkeys; kc += 64) {
     const int i0 = kc + lane, i1 = kc + 32 + lane;
     const int32_t key0 = next0, key1 = next1;
-    next0 = key_at(i0 + 64);  // the next chunk's keys, in flight
-    next1 = key_at(i1 + 64);
+    next0 = after0;
+    next1 = after1;
+    after0 = key_at(i0 + 128);
+    after1 = key_at(i1 + 128);
     // an element of N(v) equal to t is special whatever N(t) holds
     const bool is_t0 = i0 < nkeys && !stage_v && key0 == c.t32;
     const bool is_t1 = i1 < nkeys && !stage_v && key1 == c.t32;
     bool pend0 = i0 < nkeys && !is_t0, pend1 = i1 < nkeys && !is_t1;
     int at0 = -1, at1 = -1;  // index of the key inside L, or -1
     for (;;) {
-      const int b = wi & (sm.nbuf - 1);
-      const int32_t* w = sm.win + b * (sm.wlen + 8) + stage_off(sm, L, wi);
-      const int cnt = min(W, llen - wi * W);
-      const bool last = wi == nwin - 1;
-      const int32_t wlast = w[cnt - 1];
-      const bool go0 = pend0 && (last || key0 <= wlast);
-      const bool go1 = pend1 && (last || key1 <= wlast);
+      const bool go0 = pend0 && (wlast_inf || key0 <= wlast);
+      const bool go1 = pend1 && (wlast_inf || key1 <= wlast);
       if (go0 || go1) {
-        // fixed-depth searches over the power-of-two window (slots >= cnt read as +inf)
-        int lo0 = 0, lo1 = 0;
-        for (int st = W >> 1; st > 0; st >>= 1) {  // slots [cnt, W) hold +inf
-          lo0 += w[lo0 + st - 1] < key0 ? st : 0;
-          lo1 += w[lo1 + st - 1] < key1 ? st : 0;
-        }
-        if (lo0 < cnt && w[lo0] < key0) ++lo0;
-        if (lo1 < cnt && w[lo1] < key1) ++lo1;
-        if (go0 && lo0 < cnt && w[lo0] == key0) at0 = wi * W + lo0;
-        if (go1 && lo1 < cnt && w[lo1] == key1) at1 = wi * W + lo1;
+        // fixed-depth searches over the power-of-two window (slots [cnt, W) hold +inf)
+        int lo0, lo1;
+        window_rank2_any(W, wbase, key0, key1, lo0, lo1);
+        if (lo0 < wcnt && lds32(wbase + 4u * lo0) < key0) ++lo0;
+        if (lo1 < wcnt && lds32(wbase + 4u * lo1) < key1) ++lo1;
+        if (go0 && lo0 < wcnt && lds32(wbase + 4u * lo0) == key0) at0 = wi * W + lo0;
+        if (go1 && lo1 < wcnt && lds32(wbase + 4u * lo1) == key1) at1 = wi * W + lo1;
         pend0 = pend0 && !go0;
         pend1 = pend1 && !go1;
       }
@@ -364,6 +419,7 @@ __device__ __forceinline__ void gen_specials(const StepCtx& c, int mode, int32_t
       if (wi + sm.nbuf < nwin) stage_issue(sm, g, L, llen, wi + sm.nbuf, lane);
       ++wi;
       land(wi);
+      set_window(wi);
     }
     int32_t pos0 = -1, pos1 = -1;
     uint32_t cls0 = 0, cls1 = 0;
@@ -414,9 +470,9 @@ __device__ __forceinline__ int32_t warp_step(const GraphView& g, int64_t t, int6
   c.nv = nv;
   c.nt = g.col + bt;
   c.t32 = (int32_t)t;
-  c.ins = 0;
+  c.ins = -1;          // t's slot in S: found only by the modes that walk S
   c.has_self = false;
-  c.slen = c.dt + 1;  // |S| unless t has a self-loop; fixed below where S is walked
+  c.slen = c.dt + 1;   // |S| unless t has a self-loop; fixed where S is walked
   const uint64_t Wv = g.w ? __ldg(g.wpre + ev - 1) : (uint64_t)dv;
 
   const bool v_short = c.dv <= c.slen;
@@ -431,7 +487,7 @@ __device__ __forceinline__ int32_t warp_step(const GraphView& g, int64_t t, int6
     mode = v_short ? 0 : 1;
     if (g.hub_of) hub = __ldg(g.hub_of + (v_short ? t : v));
   }
-  if (mode == 1 || mode == 2) {  // these walk S = N(t) + {t} in order
+  if (mode == 1) {  // walks S = N(t) + {t} in order (mode 2 finds t's slot while its copies fly)
     c.ins = lower_bound32(c.nt, c.dt, c.t32);
     c.has_self = c.ins < c.dt && __ldg(c.nt + c.ins) == c.t32;
     c.slen = c.dt + (c.has_self ? 0 : 1);
@@ -458,7 +514,9 @@ __device__ __forceinline__ int32_t warp_step(const GraphView& g, int64_t t, int6
     sk.skip = seg;
     gen_specials(c, mode, hub, sm, sk, a_p, a_q, lane);
     if (seg == 0) {
-      const uint64_t T = (uint64_t)a_q * Wv + warp_sum_u64(sk.dpart);
+      const uint64_t corr = g.w ? warp_sum_u64(sk.dpart)
+                                : (uint64_t)(sk.cnt - (sk.ord_t >= 0 ? 1 : 0)) * d1 + (sk.ord_t >= 0 ? d2 : 0ull);
+      const uint64_t T = (uint64_t)a_q * Wv + corr;
       if (T == 0) return -1;
       r = scale_draw(u, T);
     }
