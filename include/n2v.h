@@ -80,10 +80,13 @@ extern "C" {
 
 /* ---- tuning ---------------------------------------------------------------- */
 typedef struct n2v_tune {
-  int32_t block_threads;   /* threads per block of the binned/persistent kernels (64..1024, x32) */
-  int32_t blocks_per_sm;   /* resident blocks per SM for the persistent grid; 0 = occupancy max.
-                              The persistent kernel is compiled for 2, 3 (default) or 4 resident
-                              256-thread blocks; 2 and >= 4 select those register budgets.      */
+  int32_t block_threads;   /* threads per block of the binned/persistent kernels (64..256, x32;
+                              default 128)                                                    */
+  int32_t blocks_per_sm;   /* resident blocks per SM for the persistent grid; 0 = 20 resident
+                              warps per SM where block_threads divides that, else 16, capped by
+                              shared memory.  The persistent kernel is compiled for 128, 96, 80
+                              and 64 registers a thread; the resident warps per SM (<= 16, 20,
+                              24, more) select the budget.                                    */
   int32_t thread_max_deg;  /* a step runs on one lane when deg(v) and deg(t) are <= this      */
   int32_t smem_specials;   /* per-warp shared-memory slots for the special positions of a step */
   int32_t hub_count;       /* vertices (largest degree first) with a hashed neighbour set     */
@@ -310,7 +313,9 @@ int n2v_selftest_timeout(const n2v_graph* g, int64_t limit_cycles, void* stream)
 /* Static text for a status code. */
 const char* n2v_strerror(int code);
 
-/* Number of SMs and the persistent grid the handle would launch. */
+/* Number of SMs and the persistent grid the handle would launch: blocks of
+ * 128 threads, as many per SM as the tuning's resident warps ask for (20 by
+ * default) and shared memory holds. */
 int n2v_launch_shape(const n2v_graph* g, int32_t* sms, int32_t* blocks, int32_t* threads);
 
 #ifdef __cplusplus

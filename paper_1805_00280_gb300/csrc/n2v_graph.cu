@@ -217,7 +217,7 @@ static int build_hubs(n2v_graph* g, const AuxLayout& L, cudaStream_t s) {
 }
 
 static bool tune_ok(const n2v_tune& t) {
-  if (t.block_threads < 64 || t.block_threads > 1024 || t.block_threads % 32) return false;
+  if (t.block_threads < 64 || t.block_threads > 256 || t.block_threads % 32) return false;
   if (t.blocks_per_sm < 0 || t.thread_max_deg < 0 || t.smem_specials < 32 || t.smem_specials > 8192) return false;
   if (t.hub_count < 0 || t.hub_min_degree < 0 || t.chunk_walkers < 0 || t.hub_budget_mb < 0) return false;
   if (t.stage_window != 0 && (t.stage_window < 64 || t.stage_window > 4096 || (t.stage_window & (t.stage_window - 1))))
@@ -239,7 +239,7 @@ extern "C" {
 void n2v_tune_default(n2v_tune* t) {
   if (!t) return;
   memset(t, 0, sizeof(*t));
-  t->block_threads = 256;
+  t->block_threads = 128;
   t->blocks_per_sm = 0;
   t->thread_max_deg = 16;
   t->smem_specials = 256;

@@ -52,6 +52,9 @@ struct WalkJob {
   uint32_t w_min, w_max;   // extreme edge weights of the graph
 };
 
+// Threads per block of the persistent kernels (the sampler and the serving tick).
+constexpr int kPersistThreads = 128;
+
 // Tuning resolved for a launch.
 struct LaunchCfg {
   int block_threads;
@@ -62,7 +65,7 @@ struct LaunchCfg {
   int stream_ratio;    // x10
   int spill_specials;  // per warp, in the device workspace (persistent sampler only)
   int stage_buffers;   // staging windows per warp (2 or 4)
-  int minb;            // persistent kernel instance: resident 256-thread blocks per SM it is compiled for
+  int minb;            // persistent kernel instance: resident 128-thread blocks per SM it is compiled for
 };
 
 // Shared memory of one warp: four mbarrier slots (32 bytes), the specials

@@ -35,9 +35,10 @@ struct DevSlice {
   uint32_t pad;
 };
 
-__global__ void __launch_bounds__(256, 3) k_serve(GraphView g, const DevSlice* __restrict__ slices, int nslices,
-                                                  int64_t total_slots, unsigned long long* __restrict__ counter,
-                                                  LaunchCfg L, uint32_t* __restrict__ spill, uint32_t* status) {
+// 96 registers a thread: five resident 128-thread blocks per SM (the default grid)
+__global__ void __launch_bounds__(kPersistThreads, 5)
+    k_serve(GraphView g, const DevSlice* __restrict__ slices, int nslices, int64_t total_slots,
+            unsigned long long* __restrict__ counter, LaunchCfg L, uint32_t* __restrict__ spill, uint32_t* status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;

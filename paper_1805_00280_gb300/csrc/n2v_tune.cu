@@ -17,10 +17,13 @@ struct Axis {
   std::vector<int32_t> values;
 };
 
-static size_t ws_for(const n2v_graph* g, int64_t sample, int32_t l, int blocks_per_sm, int spill) {
+// resident warps per SM tried by the descent (blocks_per_sm follows from block_threads)
+static const int kWarpTargets[] = {20, 16, 24};
+
+static size_t ws_for(const n2v_graph* g, int64_t sample, int32_t l, int warps_per_sm, int spill) {
   const int64_t chunks = g->tune.chunk_walkers > 0 ? (sample + g->tune.chunk_walkers - 1) / g->tune.chunk_walkers : 1;
   size_t b = ((sizeof(unsigned long long) * (size_t)chunks) + 255) & ~(size_t)255;
-  b += sizeof(uint32_t) * (size_t)g->sms * (size_t)blocks_per_sm * (size_t)(g->tune.block_threads / 32) * (size_t)spill;
+  b += sizeof(uint32_t) * (size_t)g->sms * (size_t)warps_per_sm * (size_t)spill;
   (void)l;
   return b;
 }
@@ -33,8 +36,10 @@ extern "C" {
 
 int n2v_autotune_ws_bytes(const n2v_graph* g, int64_t sample, int32_t l, size_t* bytes) {
   if (!g || !bytes || sample < 1 || l < 1) return N2V_ERR_INVALID_ARG;
-  // the largest candidate grid: 4 resident blocks per SM (or the caller's larger choice)
-  *bytes = ws_for(g, sample, l, std::max(4, g->tune.blocks_per_sm), g->tune.spill_specials);
+  // the largest candidate grid: 24 resident warps per SM (or the caller's larger
+  // choice, rounded up to whole 4-warp blocks of the persistent kernel)
+  const int bw = g->tune.block_threads / 32;
+  *bytes = ws_for(g, sample, l, std::max(24, (g->tune.blocks_per_sm * bw + 3) & ~3), g->tune.spill_specials);
   return N2V_OK;
 }
 
@@ -70,14 +75,21 @@ int n2v_autotune(n2v_graph* g, const int32_t* starts, int64_t n_starts, int32_t 
 
   std::vector<Axis> axes;
   axes.push_back({&n2v_tune::stage_window, {512, 1024, 256}});
-  axes.push_back({&n2v_tune::blocks_per_sm, {3, 4}});
+  {
+    const int bw = start.block_threads / 32;
+    Axis blocks{&n2v_tune::blocks_per_sm, {}};
+    for (int w : kWarpTargets)
+      if (w % bw == 0) blocks.values.push_back(w / bw);
+    if (blocks.values.empty()) blocks.values.push_back(std::max(1, 16 / bw));
+    axes.push_back(blocks);
+  }
   axes.push_back({&n2v_tune::stream_ratio, {15, 40, 100}});
   axes.push_back({&n2v_tune::thread_max_deg, {0, 16, 48}});
   axes.push_back({&n2v_tune::stage_buffers, {2, 4}});
   if (start.hub_count > 0) axes.push_back({&n2v_tune::hub_count, {0, start.hub_count}});
 
   n2v_tune cur = start;
-  if (cur.blocks_per_sm <= 0) cur.blocks_per_sm = 3;
+  if (cur.blocks_per_sm <= 0) cur.blocks_per_sm = axes[1].values[0];
   float cur_ms = 0.f;
   rc = measure(cur, &cur_ms);
   for (size_t a = 0; a < axes.size() && rc == N2V_OK; ++a) {
@@ -85,7 +97,7 @@ int n2v_autotune(n2v_graph* g, const int32_t* starts, int64_t n_starts, int32_t 
       if (cur.*(axes[a].field) == val) continue;
       n2v_tune cand = cur;
       cand.*(axes[a].field) = val;
-      // 4 windows of 1024 do not fit beside 3 resident blocks: skip that corner
+      // four windows of 1024 per warp do not fit beside 20 or more resident warps: skip that corner
       if (cand.stage_buffers * (cand.stage_window + 8) * 4 * (cand.block_threads / 32) * cand.blocks_per_sm > 200 * 1024)
         continue;
       float ms = 0.f;

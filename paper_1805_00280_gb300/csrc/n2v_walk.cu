@@ -92,9 +92,9 @@ __global__ void __launch_bounds__(256) k_binned_step(GraphView g, WalkJob J, int
 // by degree as above.  Walkers are independent (FN-Multi's observation,
 // Section 3.4), so the order in which warps take them does not change any row.
 template <int MINB>
-__global__ void __launch_bounds__(256, MINB) k_persistent(GraphView g, WalkJob J,
-                                                          unsigned long long* __restrict__ counter, LaunchCfg L,
-                                                          uint32_t* __restrict__ spill) {
+__global__ void __launch_bounds__(kPersistThreads, MINB)
+    k_persistent(GraphView g, WalkJob J, unsigned long long* __restrict__ counter, LaunchCfg L,
+                 uint32_t* __restrict__ spill) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
@@ -194,24 +194,29 @@ __global__ void k_selftest_wait(uint32_t* status, long long limit) {
 
 static int smem_per_block(const LaunchCfg& c) { return (c.block_threads / 32) * warp_smem_bytes(c); }
 
-// The persistent kernel is compiled for 2, 3 or 4 resident 256-thread blocks
-// per SM (128, 80 or 64 registers per thread); blocks_per_sm picks one.
-static int persistent_minb(const n2v_tune& t) { return t.blocks_per_sm >= 4 ? 4 : (t.blocks_per_sm == 2 ? 2 : 3); }
+// The persistent kernel is compiled for 4, 5, 6 or 8 resident blocks of 128
+// threads per SM: 128, 96, 80 or 64 registers a thread (each of the SM's four
+// schedulers holds one warp of every block in its 16384 registers).  Fewer
+// registers than the code wants spill to local memory; more warps hide more
+// latency.
+static int persistent_minb(int per_sm) { return per_sm <= 4 ? 4 : per_sm <= 5 ? 5 : per_sm <= 6 ? 6 : 8; }
 
 static const void* persistent_fn(int minb) {
   switch (minb) {
-    case 2: return (const void*)k_persistent<2>;
     case 4: return (const void*)k_persistent<4>;
-    default: return (const void*)k_persistent<3>;
+    case 6: return (const void*)k_persistent<6>;
+    case 8: return (const void*)k_persistent<8>;
+    default: return (const void*)k_persistent<5>;
   }
 }
 
 static void launch_persistent(const LaunchCfg& L, int smem, cudaStream_t s, const GraphView& g, const WalkJob& J,
                               unsigned long long* counter, uint32_t* spill) {
   switch (L.minb) {
-    case 2: k_persistent<2><<<L.blocks, L.block_threads, smem, s>>>(g, J, counter, L, spill); break;
     case 4: k_persistent<4><<<L.blocks, L.block_threads, smem, s>>>(g, J, counter, L, spill); break;
-    default: k_persistent<3><<<L.blocks, L.block_threads, smem, s>>>(g, J, counter, L, spill); break;
+    case 6: k_persistent<6><<<L.blocks, L.block_threads, smem, s>>>(g, J, counter, L, spill); break;
+    case 8: k_persistent<8><<<L.blocks, L.block_threads, smem, s>>>(g, J, counter, L, spill); break;
+    default: k_persistent<5><<<L.blocks, L.block_threads, smem, s>>>(g, J, counter, L, spill); break;
   }
 }
 
@@ -224,12 +229,27 @@ LaunchCfg resolve_launch(const n2v_graph* g, int variant) {
   c.stream_ratio = g->tune.stream_ratio;
   c.spill_specials = g->tune.spill_specials;
   c.stage_buffers = g->tune.stage_buffers;
-  c.minb = persistent_minb(g->tune);
+  if (variant == N2V_PERSISTENT) {
+    // 128-thread blocks; the tuning's resident warps per SM (20 by default),
+    // as many as shared memory holds
+    c.block_threads = kPersistThreads;
+    const int warps = g->tune.blocks_per_sm > 0 ? g->tune.blocks_per_sm * (g->tune.block_threads / 32) : 20;
+    int per_sm = std::max(1, (warps + 3) / 4);
+    const int smem = smem_per_block(c);
+    const void* fn = persistent_fn(8);  // the fewest registers: only shared memory limits it
+    if (smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, c.block_threads, smem) == cudaSuccess && occ > 0)
+      per_sm = std::min(per_sm, occ);
+    c.minb = persistent_minb(per_sm);
+    c.blocks = g->sms * per_sm;
+    return c;
+  }
   const int smem = smem_per_block(c);
   int per_sm = g->tune.blocks_per_sm;
   if (per_sm <= 0) {
     per_sm = 1;
-    const void* fn = variant == N2V_PERSISTENT ? persistent_fn(c.minb) : (const void*)k_binned_step;
+    const void* fn = (const void*)k_binned_step;
     if (smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, c.block_threads, smem) == cudaSuccess && occ > 0)

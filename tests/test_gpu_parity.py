@@ -33,6 +33,10 @@ TUNES = {
     "stage4": dict(thread_max_deg=0, stream_ratio=100_000, stage_window=64, stage_buffers=4),
     # specials kept 32 at a time: the enumeration restarts segment by segment
     "segments": dict(thread_max_deg=0, smem_specials=32, spill_specials=0, stage_window=64, stream_ratio=100_000),
+    # the persistent kernel's other register budgets: 16, 24 and 32 resident warps per SM
+    "warps16": dict(blocks_per_sm=4),
+    "warps24": dict(block_threads=256, blocks_per_sm=3),
+    "warps32": dict(blocks_per_sm=8, stage_window=512),
 }
 
 
@@ -150,7 +154,7 @@ def test_rmat14_full_output(weighted, pq):
     p, q = pq
     starts = np.arange(g.n, dtype=np.int32)
     want = oracle_rows(g, starts, 20, p, q, 77, np.arange(g.n * 2))
-    for tname in ["default", "hubs", "spill", "probe", "stage", "stage4", "segments"]:
+    for tname in ["default", "hubs", "spill", "probe", "stage", "stage4", "segments", "warps16", "warps24", "warps32"]:
         graph = n2v.Graph.from_csr(g, tune=n2v.default_tune(**TUNES[tname]))
         for v in VARIANTS:
             got = gpu_rows(g, starts, 2, 20, p, q, 77, v, graph=graph)
@@ -289,3 +293,19 @@ def test_bounded_wait_times_out_cleanly():
     starts = np.arange(g.n, dtype=np.int32)
     want = oracle_rows(g, starts, 5, 1.0, 1.0, 2, np.arange(g.n))
     np.testing.assert_array_equal(gpu_rows(g, starts, 1, 5, 1.0, 1.0, 2, "persistent", graph=graph), want)
+
+
+def test_persistent_launch_shape():
+    """128-thread blocks; 20 resident warps per SM by default, the tuning's count otherwise, capped by shared memory."""
+    g = G.er(1000, 5000, 1)
+    shapes = {}
+    for name, tune in [("default", {}), ("w16", dict(blocks_per_sm=4)), ("w24", dict(block_threads=256, blocks_per_sm=3)),
+                       ("w32", dict(blocks_per_sm=8, stage_window=512)), ("w32big", dict(blocks_per_sm=8))]:
+        graph = n2v.Graph.from_csr(g, tune=n2v.default_tune(**tune))
+        sms, blocks, threads = n2v.n2v_launch_shape(graph.handle)
+        assert threads == 128 and blocks % sms == 0
+        shapes[name] = blocks // sms
+    assert shapes["default"] == 5 and shapes["w16"] == 4 and shapes["w24"] == 6 and shapes["w32"] == 8
+    # 32 warps of two 1024-element windows each (9312 bytes a warp) do not fit in one SM's shared memory
+    assert shapes["w32big"] < 8
+
