@@ -186,13 +186,16 @@ __device__ __forceinline__ void window_rank2(uint32_t base, int32_t key0, int32_
   lo1 = b;
 }
 
-__device__ __forceinline__ void window_rank2_any(int W, uint32_t base, int32_t key0, int32_t key1, int& lo0, int& lo1) {
-  if (W == 1024) {
+// The same search over a window of depth slots (a power of two): unrolled for
+// full 1024-element windows, a loop for every other depth.
+__device__ __forceinline__ void window_rank2_any(int depth, uint32_t base, int32_t key0, int32_t key1, int& lo0,
+                                                 int& lo1) {
+  if (depth == 1024) {
     window_rank2<1024>(base, key0, key1, lo0, lo1);
     return;
   }
-  int a = 0, b = 0;  // other window sizes: the same search, not unrolled
-  for (int st = W >> 1; st > 0; st >>= 1) {
+  int a = 0, b = 0;
+  for (int st = depth >> 1; st > 0; st >>= 1) {
     const int32_t v0 = lds32(base + 4u * (uint32_t)(a + st - 1));
     const int32_t v1 = lds32(base + 4u * (uint32_t)(b + st - 1));
     a += v0 < key0 ? st : 0;
@@ -361,26 +364,30 @@ __device__ __forceinline__ void gen_specials(StepCtx& c, int mode, int32_t hub, 
   // two keys per lane and chunk (keys kc + lane and kc + 32 + lane): two
   // independent search chains in flight per lane
   auto key_at = [&](int i) -> int32_t { return i < nkeys ? (stage_v ? s_at(c, i) : __ldg(c.nv + i)) : 0; };
-  // after a window lands: a short (last) window is padded to wlen with +inf
-  // so that the fixed-depth search needs no bounds test
+  // search depth of a window holding cnt elements: the next power of two
+  auto depth_of = [](int cnt) { return cnt <= 1 ? 1 : 1 << (32 - __clz(cnt - 1)); };
+  // after a window lands: a short (last) window is padded with +inf up to its
+  // search depth, so that the fixed-depth search needs no bounds test
   auto land = [&](int wj) {
     stage_wait(sm, wj & (sm.nbuf - 1));
     const int cnt = min(W, llen - wj * W);
-    if (cnt < W) {
+    const int depth = depth_of(cnt);
+    if (cnt < depth) {
       int32_t* w = sm.win + (wj & (sm.nbuf - 1)) * (sm.wlen + 8) + stage_off(sm, L, wj);
-      for (int q = cnt + lane; q < W; q += 32) w[q] = INT32_MAX;
+      for (int q = cnt + lane; q < depth; q += 32) w[q] = INT32_MAX;
       __syncwarp();
     }
   };
   // keys two chunks ahead are in flight while a chunk is searched
   // the resident window: shared address, length, last element (+inf for the last window)
   uint32_t wbase = 0;
-  int wcnt = 0;
+  int wcnt = 0, wdepth = 0;
   int32_t wlast = 0;
   bool wlast_inf = false;
   auto set_window = [&](int wj) {
     wbase = smem_addr(sm.win + (wj & (sm.nbuf - 1)) * (sm.wlen + 8) + stage_off(sm, L, wj));
     wcnt = min(W, llen - wj * W);
+    wdepth = depth_of(wcnt);
     wlast_inf = wj == nwin - 1;
     wlast = lds32(wbase + 4u * (uint32_t)(wcnt - 1));
   };
@@ -404,9 +411,9 @@ __device__ __forceinline__ void gen_specials(StepCtx& c, int mode, int32_t hub, 
       const bool go0 = pend0 && (wlast_inf || key0 <= wlast);
       const bool go1 = pend1 && (wlast_inf || key1 <= wlast);
       if (go0 || go1) {
-        // fixed-depth searches over the power-of-two window (slots [cnt, W) hold +inf)
+        // fixed-depth searches over the power-of-two window (slots [wcnt, wdepth) hold +inf)
         int lo0, lo1;
-        window_rank2_any(W, wbase, key0, key1, lo0, lo1);
+        window_rank2_any(wdepth, wbase, key0, key1, lo0, lo1);
         if (lo0 < wcnt && lds32(wbase + 4u * lo0) < key0) ++lo0;
         if (lo1 < wcnt && lds32(wbase + 4u * lo1) < key1) ++lo1;
         if (go0 && lo0 < wcnt && lds32(wbase + 4u * lo0) == key0) at0 = wi * W + lo0;
