@@ -55,6 +55,9 @@ def parse_args():
     ap.add_argument("--compare-rounds", type=int, default=1,
                     help="the compared variants run the first R rounds (every start vertex R times)")
     ap.add_argument("--compare-walks", type=int, default=1 << 22, help="cap on the walks of the compared variants")
+    ap.add_argument("--ingest-ncu", nargs=2, metavar=("LAUNCH_CSV", "BENCH_JSON"), default=None,
+                    help="write profiles/traffic_<variant>_<workload>.json from an ncu launch list (with DRAM bytes) "
+                         "of a bench run with --no-cpu --no-e2e, and that run's JSON line")
     ap.add_argument("--cuda-graph", type=int, default=-1, help="record the launches as a CUDA graph (-1: per workload)")
     ap.add_argument("--autotune", type=int, default=1, help="tune the persistent sampler on a sample first")
     ap.add_argument("--jobs", type=int, default=10_000, help="serving workload: number of jobs")
@@ -76,12 +79,16 @@ def dist_env():
     return rank, world, local
 
 
+# the sources the sampler kernels are compiled from (the autotuner, serving
+# loop and graph loader are not part of them)
+KERNEL_SOURCES = ["paper_1805_00280_gb300/csrc/n2v_walk.cu", "paper_1805_00280_gb300/csrc/n2v_step.cuh",
+                  "paper_1805_00280_gb300/csrc/n2v_internal.cuh", "include/n2v.h"]
+
+
 def csrc_digest() -> str:
-    d = os.path.join(REPO, "paper_1805_00280_gb300", "csrc")
     h = hashlib.sha256()
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(d, f), "rb").read())
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(REPO, f), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -152,14 +159,14 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
-def ncu_traffic(workload: str, variant: str):
-    """Per-launch DRAM bytes from a committed ncu summary, if the kernels have not changed since."""
+def ncu_traffic(workload: str, variant: str, tune: dict):
+    """Per-launch DRAM bytes from a committed ncu summary, if neither the kernels nor the tuning have changed since."""
     p = os.path.join(REPO, "profiles", f"traffic_{variant}_{workload}.json")
     try:
         d = json.load(open(p))
     except Exception:
         return None
-    if d.get("csrc_sha") != csrc_digest():
+    if d.get("csrc_sha") != csrc_digest() or d.get("tune") != tune:
         return None
     return d.get("dram_bytes_per_launch")
 
@@ -304,8 +311,9 @@ def run_ours(args):
     tuned = None
     if args.autotune and args.variant == "persistent":
         t0 = time.perf_counter()
-        best, ms = n2v.autotune(graph, np.arange(g.n, dtype=np.int32), wl.l, pq[0][0], pq[0][1], wl.seed,
-                                sample=1 << 16, stream=stream)
+        # a sample that fills every resident warp many times over: 2^20 walks of 20 steps
+        best, ms = n2v.autotune(graph, np.arange(g.n, dtype=np.int32), min(wl.l, 20), pq[0][0], pq[0][1], wl.seed,
+                                sample=min(1 << 20, g.n), stream=stream)
         tuned = {"tune": best.as_dict(), "sample_ms": round(ms, 3), "tune_s": round(time.perf_counter() - t0, 2)}
         tune = best
     info = graph.info()
@@ -377,7 +385,7 @@ def run_ours(args):
     # ---- roofline of the dominant kernel (the persistent sampler: one launch per (p,q))
     peak, peak_kind = measured_peak_hbm()
     achieved = sum(abytes) / (sum(mean_launch_ms) / 1e3) / 1e9
-    dram = ncu_traffic(wl.name, args.variant)
+    dram = ncu_traffic(wl.name, args.variant, tune.as_dict())
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": dram, "peak_kind": peak_kind,
                 "algorithmic_bytes_per_launch": [int(b) for b in abytes],
@@ -540,7 +548,8 @@ def run_serving(args):
     g = G.workload_graph(wl.name)
     gen_s = time.perf_counter() - t0
     graph = n2v.Graph.from_csr(g, device=dev)
-    best, _ = n2v.autotune(graph, np.arange(g.n, dtype=np.int32), 40, 1.0, 1.0, 1, sample=1 << 16, stream=stream)
+    best, _ = n2v.autotune(graph, np.arange(g.n, dtype=np.int32), 20, 1.0, 1.0, 1, sample=min(1 << 20, g.n),
+                           stream=stream)
     jobs = serving_jobs(g.n, args.jobs)
     for jb in jobs:
         jb["starts"] = G.uniform(jb["seed"], jb["stream"], g.n, jb["size"]).astype(np.int32)
@@ -637,9 +646,53 @@ def run_serving(args):
     print(json.dumps(line), flush=True)
 
 
+def ingest_ncu(csv_path: str, json_path: str) -> None:
+    """Per-launch DRAM traffic of the timed launches, from a one-pass ncu launch list.
+
+    The run must be ``bench.py ... --no-cpu --no-e2e`` (one variant timed, then the
+    compared variants with the timed one first): its sampler launches are the
+    autotuner's, then warm-up x jobs, then steps x jobs (timed), then two per job
+    for the comparison.
+    """
+    import csv
+
+    line = [x for x in open(json_path) if x.startswith("{")][-1]
+    d = json.loads(line)
+    cfg = d["config"]
+    npq, steps = len(cfg["pq"]), d["steps"]
+    kernel = d["roofline"]["kernel"]
+    rows = list(csv.reader(open(csv_path)))
+    hi = next(i for i, r in enumerate(rows) if "Metric Name" in r)
+    h = rows[hi]
+    I, K, MN, MV = (h.index(x) for x in ("ID", "Kernel Name", "Metric Name", "Metric Value"))
+    by = {}
+    for r in rows[hi + 1:]:
+        if len(r) > MV and kernel in r[K]:
+            by.setdefault(int(r[I]), {})[r[MN]] = float(r[MV].replace(",", ""))
+    launches = [by[i] for i in sorted(by)]
+    timed = launches[-(2 + steps) * npq: -2 * npq]
+    traffic = [x["dram__bytes_read.sum"] + x["dram__bytes_write.sum"] for x in timed]
+    out = {"workload": cfg["workload"], "variant": cfg["variant"], "kernel": kernel, "csrc_sha": csrc_digest(),
+           "tune": cfg["tune"], "pq": cfg["pq"], "walks_per_launch": cfg["walks_per_gpu"],
+           "dram_bytes_per_launch": int(statistics.mean(traffic)),
+           "per_launch": [{"dram_read": int(x["dram__bytes_read.sum"]), "dram_write": int(x["dram__bytes_write.sum"]),
+                           "ncu_ms": x["gpu__time_duration.sum"] / 1e6} for x in timed],
+           "algorithmic_bytes_per_launch": d["roofline"]["algorithmic_bytes_per_launch"],
+           "source": "ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum "
+                     "--clock-control none (one pass), timed launches of bench.py --steps %d --warmup %d "
+                     "--no-cpu --no-e2e" % (steps, d["warmup"])}
+    p = os.path.join(REPO, "profiles", f"traffic_{cfg['variant']}_{cfg['workload']}.json")
+    with open(p, "w") as f:
+        json.dump(out, f, indent=1)
+        f.write("\n")
+    print(json.dumps({"written": p, "dram_bytes_per_launch": out["dram_bytes_per_launch"]}))
+
+
 def main():
     args = parse_args()
-    if args.impl == "reference":
+    if args.ingest_ncu:
+        ingest_ncu(*args.ingest_ncu)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.workload == "rmat24serve":
         run_serving(args)

@@ -239,7 +239,9 @@ int n2v_autotune_ws_bytes(const n2v_graph* g, int64_t sample, int32_t l, size_t*
  * thread_max_deg, stage_buffers and (if the graph was loaded with hubs)
  * hub_count, each candidate timed with CUDA events on walks [0, sample) of
  * the job "one walk from each of starts[0..sample)" (the caller should pass a
- * representative random sample of its start vertices).  Every tuning gives
+ * representative random sample of its start vertices).  A candidate is
+ * timed as the faster of two runs (after one untimed run) and replaces the
+ * current tuning only when it is at least 2% faster.  Every tuning gives
  * the same rows, so only time is compared.  `walks` (device int32
  * [sample][l]) and `ws` (n2v_autotune_ws_bytes) are scratch.  Synchronises
  * `stream`.  On success the best tuning is applied to g and returned in
