@@ -43,7 +43,8 @@ def parse_args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rmat20")
     ap.add_argument("--variant", default="persistent", choices=["persistent", "binned", "plain"])
-    ap.add_argument("--compare", default="plain,binned", help="variants timed once beside the main one")
+    ap.add_argument("--compare", default="plain,binned,stored",
+                    help="variants timed once beside the main one (stored: the stored-table baseline)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle baseline leg")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -55,6 +56,7 @@ def parse_args():
     ap.add_argument("--compare-rounds", type=int, default=1,
                     help="the compared variants run the first R rounds (every start vertex R times)")
     ap.add_argument("--compare-walks", type=int, default=1 << 22, help="cap on the walks of the compared variants")
+    ap.add_argument("--sweep", default="", help="run every workload of a sweep (skew, wec), one JSON line each")
     ap.add_argument("--ingest-ncu", nargs=2, metavar=("LAUNCH_CSV", "BENCH_JSON"), default=None,
                     help="write profiles/traffic_<variant>_<workload>.json from an ncu launch list (with DRAM bytes) "
                          "of a bench run with --no-cpu --no-e2e, and that run's JSON line")
@@ -396,7 +398,7 @@ def run_ours(args):
     #      `compare_rounds` times), beside the main variant on the same rows
     compare = {}
     Wc = min(W, n_start * max(1, args.compare_rounds), args.compare_walks)
-    names = [v for v in args.compare.split(",") if v and v != args.variant]
+    names = [v for v in args.compare.split(",") if v and v != args.variant and v != "stored"]
     if names:
         tmp = torch.empty((Wc, l), dtype=torch.int32, device=dev)
         sub = {}
@@ -424,6 +426,10 @@ def run_ours(args):
         compare = {"walks_per_pq": Wc, "variants": sub}
         if "plain" in sub:
             compare["speedup_over_plain_same_rows"] = sub[args.variant]["value"] / sub["plain"]["value"]
+    if "stored" in args.compare.split(","):
+        compare.setdefault("walks_per_pq", Wc)
+        compare["stored"] = stored_compare(n2v, graph, g, starts, n_start, r_total, l, pq, wl.seed, walk_begin, Wc,
+                                           outs, stream, dev, world, flush)
 
     # ---- end to end through the C ABI with host buffers
     e2e = None
@@ -498,6 +504,9 @@ def run_ours(args):
         "parity": parity,
         "wall_s_timed": wall,
     }
+    if args.sweep:
+        line["sweep"] = args.sweep
+        line["degree_bins"] = degree_bins(graph, info, outs[0])
     if rank == 0:
         print(json.dumps(line), flush=True)
     graph.close()
@@ -646,7 +655,73 @@ def run_serving(args):
     print(json.dumps(line), flush=True)
 
 
-def ingest_ncu(csv_path: str, json_path: str) -> None:
+def degree_bins(graph, info, rows) -> dict:
+    """Vertices and walk visits per degree bin ([0]: degree 0, [i]: [2^(i-1), 2^i)), as in the
+    degree-vs-frequency view of Section 3.3: how often the walks stand on vertices of each degree."""
+    import torch
+
+    rp = graph.row_ptr
+    visits = torch.zeros(34, dtype=torch.int64, device=rp.device)
+    flat = rows.reshape(-1)
+    for c0 in range(0, flat.numel(), 1 << 26):
+        v = flat[c0:c0 + (1 << 26)].to(torch.int64)
+        v = v[v >= 0]
+        d = rp[v + 1] - rp[v]
+        b = torch.where(d > 0, torch.floor(torch.log2(d.clamp(min=1).to(torch.float64))).to(torch.int64) + 1,
+                        torch.zeros_like(d))
+        visits += torch.bincount(b, minlength=34)[:34]
+    vs = [int(x) for x in info.deg_hist]
+    last = max([i for i in range(34) if vs[i]] + [0]) + 1
+    return {"vertices": vs[:last], "visits": [int(x) for x in visits.cpu()][:last]}
+
+
+def stored_compare(n2v, graph, g, starts, n_start, r_total, l, pq, seed, walk_begin, Wc, outs, stream, dev, world,
+                   flush):
+    """The stored-table baseline (Section 3.2, Eq. 1) beside the on-the-fly sampler.
+
+    Reports the table's bytes against the graph's, and where the table fits in
+    half the free device memory, its build time and its walk rate on the same
+    rows (which must be identical)."""
+    import torch
+
+    tbytes, entries = n2v.n2v_stored_bytes(graph.handle, stream)
+    gbytes = 8 * (g.n + 1) + 4 * g.nnz + (12 * g.nnz if g.w is not None else 0)
+    res = {"table_bytes": tbytes, "eq1_bytes": 8 * entries, "graph_bytes": gbytes,
+           "table_over_graph": tbytes / gbytes}
+    free, _ = torch.cuda.mem_get_info(dev)
+    if tbytes > free // 2:
+        res["fits"] = False
+        return res
+    res["fits"] = True
+    tmp = torch.empty((Wc, l), dtype=torch.int32, device=dev)
+    build_ms, ms, same, tr = [], [], True, 0
+    for i in range(len(pq)):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        a.record(stream)
+        table = n2v.StoredTable(graph, pq[i][0], pq[i][1], stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        build_ms.append(a.elapsed_time(b))
+        launch = lambda: n2v.n2v_stored_walk(graph.handle, table.buf, starts, n_start, r_total, l, seed, walk_begin,
+                                             Wc, tmp, stream)
+        launch()  # warm-up
+        torch.cuda.synchronize(dev)
+        flush.fill_(7)
+        a.record(stream)
+        launch()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        ms.append(a.elapsed_time(b))
+        same &= bool(torch.equal(tmp, outs[i][:Wc]))
+        tr += n2v.traffic(graph, starts, walk_begin, tmp)[0]
+        del table
+    res.update({"value": tr * world / (sum(ms) / 1e3), "unit": UNIT, "ms": sum(ms), "build_ms": build_ms,
+                "bit_identical_to_timed": same})
+    return res
+
+
+def ingest_ncu(csv_path: str, json_path: str, out_dir: str | None = None) -> str:
     """Per-launch DRAM traffic of the timed launches, from a one-pass ncu launch list.
 
     The run must be ``bench.py ... --no-cpu --no-e2e`` (one variant timed, then the
@@ -681,17 +756,26 @@ def ingest_ncu(csv_path: str, json_path: str) -> None:
            "source": "ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum "
                      "--clock-control none (one pass), timed launches of bench.py --steps %d --warmup %d "
                      "--no-cpu --no-e2e" % (steps, d["warmup"])}
-    p = os.path.join(REPO, "profiles", f"traffic_{cfg['variant']}_{cfg['workload']}.json")
+    p = os.path.join(out_dir or os.path.join(REPO, "profiles"), f"traffic_{cfg['variant']}_{cfg['workload']}.json")
     with open(p, "w") as f:
         json.dump(out, f, indent=1)
         f.write("\n")
     print(json.dumps({"written": p, "dram_bytes_per_launch": out["dram_bytes_per_launch"]}))
+    return p
 
 
 def main():
     args = parse_args()
     if args.ingest_ncu:
         ingest_ncu(*args.ingest_ncu)
+    elif args.sweep:
+        from paper_1805_00280_gb300 import graphs as G
+
+        if args.gpus > 1 or int(os.environ.get("WORLD_SIZE", "1")) > 1:
+            raise SystemExit("--sweep runs on one GPU")
+        for name in G.SWEEPS[args.sweep]:
+            args.workload = name
+            run_ours(args)
     elif args.impl == "reference":
         run_reference(args)
     elif args.workload == "rmat24serve":

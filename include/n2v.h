@@ -315,6 +315,32 @@ int n2v_selftest_timeout(const n2v_graph* g, int64_t limit_cycles, void* stream)
 /* Static text for a status code. */
 const char* n2v_strerror(int code);
 
+/* ---- stored transition tables (the baseline the paper avoids) ------------------
+ * Section 3.2, Eq. 1: precomputing every transition distribution takes one
+ * 8-byte value per (edge t->v, neighbour x of v) pair, 8 * sum_i d_i^2 bytes on
+ * an undirected graph.  These calls build that table for one (p, q) -- the
+ * cumulative weights C_j = sum_{i<=j} w(v,x_i) alpha(t,x_i) over N(v) for each
+ * edge, in CSR edge order -- and walk with it: a step is one binary search of
+ * r = floor(u * T / 2^64) in the stored C, so the rows equal n2v_walk's for
+ * the same (p, q, seed) bit for bit.  It exists to measure the memory and time
+ * the on-the-fly sampler saves.
+ *
+ * n2v_stored_bytes: size of the table buffer (header, per-edge offsets, scan
+ *   scratch, 8 bytes per entry) and the entry count sum_e deg(col[e]).
+ *   Synchronises `stream`.
+ * n2v_stored_build: fill a caller-owned, 256-byte-aligned device buffer of at
+ *   least n2v_stored_bytes bytes for (p, q).  N2V_ERR_NO_MEM if smaller,
+ *   N2V_ERR_OVERFLOW as for n2v_walk.  Asynchronous after the size check.
+ * n2v_stored_walk: walks of the job "r walks from each start" (same walk ids,
+ *   draws and output layout as n2v_walk), with the (p, q) the table was built
+ *   for.  N2V_ERR_INVALID_ARG if the table was not built for this graph handle.
+ *   Reads the table header synchronously, then launches asynchronously; start
+ *   vertices out of range are reported through n2v_stream_status. */
+int n2v_stored_bytes(const n2v_graph* g, void* stream, size_t* bytes, int64_t* entries);
+int n2v_stored_build(const n2v_graph* g, double p, double q, void* table, size_t table_bytes, void* stream);
+int n2v_stored_walk(const n2v_graph* g, const void* table, const int32_t* starts, int64_t n_starts, int32_t r,
+                    int32_t l, uint64_t seed, int64_t walk_begin, int64_t walk_count, int32_t* walks, void* stream);
+
 /* Number of SMs and the persistent grid the handle would launch: blocks of
  * 128 threads, as many per SM as the tuning's resident warps ask for (20 by
  * default) and shared memory holds. */

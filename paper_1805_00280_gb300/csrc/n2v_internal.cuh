@@ -265,6 +265,7 @@ enum : int {
   kScHist = 8,  // 34 words
   kScWMin = 42,
   kScWMax = 43,
+  kScSumDeg2 = 44,  // sum over edges of deg(target): entries of a stored transition table
   kScWords = 64
 };
 

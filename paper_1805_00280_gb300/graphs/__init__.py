@@ -174,7 +174,32 @@ WORKLOADS = {
                        note="R-MAT scale 26, ef 16, r=1, l=80, p=2, q=0.5"),
     "rmat24serve": Workload("rmat24serve", dict(kind="rmat", scale=24, ef=16, seed=1), r=1, l=80,
                             pq=[], note="serving on R-MAT scale 24, ef 16"),
+    # skewed but small enough for a stored transition table (8 sum d^2 = 76 GB)
+    "rmat18": Workload("rmat18", dict(kind="rmat", scale=18, ef=16, seed=1), r=10, l=80,
+                       pq=[(1.0, 1.0), (0.25, 4.0), (4.0, 0.25)],
+                       note="R-MAT scale 18, ef 16, (.57,.19,.19,.05), r=10, l=80"),
 }
+
+
+def skew_abc(S: float) -> tuple[float, float, float]:
+    """R-MAT (a, b, c) of the Skew-S graphs (Section 5.1): b = c = 0.25 and d = S a."""
+    a = 0.5 / (1.0 + S)
+    return (a, 0.25, 0.25)
+
+
+# Skew-S: 2^22 vertices, average degree about 100 (50 generated edges per vertex,
+# symmetrised), one walk of length 80 per vertex at p = 0.5, q = 2 (Section 5.1)
+for _S in (1, 2, 3, 4, 5):
+    WORKLOADS[f"skew{_S}"] = Workload(f"skew{_S}", dict(kind="rmat", scale=22, ef=50, seed=1, abc=skew_abc(_S)),
+                                      r=1, l=80, pq=[(0.5, 2.0)],
+                                      note=f"Skew-{_S}: R-MAT scale 22, ef 50, d = {_S} a, b = c = 0.25, r=1, l=80")
+# WeC-K: 2^K vertices, about 100 x 2^K adjacency entries, (a, b, c, d) = (.18, .25, .25, .32)
+for _K in (20, 21, 22, 23):
+    WORKLOADS[f"wec{_K}"] = Workload(f"wec{_K}", dict(kind="rmat", scale=_K, ef=50, seed=1, abc=(0.18, 0.25, 0.25)),
+                                     r=1, l=80, pq=[(0.5, 2.0)],
+                                     note=f"WeC-{_K}: R-MAT scale {_K}, ef 50, (.18,.25,.25,.32), r=1, l=80")
+
+SWEEPS = {"skew": [f"skew{S}" for S in (1, 2, 3, 4, 5)], "wec": [f"wec{K}" for K in (20, 21, 22, 23)]}
 
 
 def make_graph(spec: dict, threads: int | None = None) -> CSR:

@@ -123,6 +123,9 @@ def lib() -> ctypes.CDLL:
         L.n2v_serve_stats.argtypes = [vp, P(n2v_serve_stats_t)]
         L.n2v_serve_destroy.argtypes = [vp]
         L.n2v_serve_destroy.restype = None
+        L.n2v_stored_bytes.argtypes = [vp, vp, P(sz), P(i64)]
+        L.n2v_stored_build.argtypes = [vp, dbl, dbl, vp, sz, vp]
+        L.n2v_stored_walk.argtypes = [vp, vp, vp, i64, i32, i32, u64, i64, i64, vp, vp]
         L.n2v_autotune_ws_bytes.argtypes = [vp, i64, i32, P(sz)]
         L.n2v_autotune.argtypes = [vp, vp, i64, i32, dbl, dbl, u64, i64, vp, vp, sz, vp, P(n2v_tune),
                                    P(ctypes.c_float)]
@@ -264,6 +267,25 @@ def n2v_autotune(handle: int, starts, n_starts: int, l: int, p: float, q: float,
     _check(lib().n2v_autotune(handle, _ptr(starts), n_starts, l, p, q, seed, sample, _ptr(walks), _ptr(ws), ws_bytes,
                               _stream(stream), ctypes.byref(best), ctypes.byref(ms)), "n2v_autotune")
     return best, ms.value
+
+
+def n2v_stored_bytes(handle: int, stream=None) -> tuple[int, int]:
+    """(table buffer bytes, entries) of a stored transition table for this graph (synchronises)."""
+    b, e = ctypes.c_size_t(), ctypes.c_int64()
+    _check(lib().n2v_stored_bytes(handle, _stream(stream), ctypes.byref(b), ctypes.byref(e)), "n2v_stored_bytes")
+    return int(b.value), int(e.value)
+
+
+def n2v_stored_build(handle: int, p: float, q: float, table, stream=None) -> None:
+    nbytes = table.numel() * table.element_size()
+    _check(lib().n2v_stored_build(handle, p, q, _ptr(table), nbytes, _stream(stream)), "n2v_stored_build")
+
+
+def n2v_stored_walk(handle: int, table, starts, n_starts: int, r: int, l: int, seed: int, walk_begin: int,
+                    walk_count: int, walks, stream=None) -> None:
+    rc = lib().n2v_stored_walk(handle, _ptr(table), _ptr(starts), n_starts, r, l, seed, walk_begin, walk_count,
+                               _ptr(walks), _stream(stream))
+    _check(rc, "n2v_stored_walk")
 
 
 def n2v_serve_cfg_default() -> n2v_serve_cfg:
@@ -414,6 +436,31 @@ def autotune(graph: Graph, starts, l: int, p: float, q: float, seed: int = 1, sa
     best, ms = n2v_autotune(graph.handle, sub, sub.numel(), l, p, q, seed, sub.numel(), walks, ws, stream)
     graph.tune = best
     return best, ms
+
+
+class StoredTable:
+    """A stored transition table of the graph for one (p, q), in a torch buffer on the graph's device."""
+
+    def __init__(self, graph: Graph, p: float, q: float, stream=None):
+        self.graph = graph
+        self.p, self.q = p, q
+        self.nbytes, self.entries = n2v_stored_bytes(graph.handle, stream)
+        self.buf = torch.empty(self.nbytes // 8 + 32, dtype=torch.int64, device=graph.row_ptr.device)
+        n2v_stored_build(graph.handle, p, q, self.buf, stream)
+
+
+def stored_walk(graph: Graph, table: StoredTable, starts, r: int, l: int, seed: int, walk_begin: int = 0,
+                walk_count: int | None = None, out=None, stream=None) -> torch.Tensor:
+    """Walks [walk_count, l] sampled from a stored table (same rows as walk() with the table's p, q)."""
+    dev = graph.row_ptr.device
+    starts = torch.as_tensor(starts, dtype=torch.int32).to(dev).contiguous()
+    n_starts = int(starts.numel())
+    if walk_count is None:
+        walk_count = n_starts * r - walk_begin
+    if out is None:
+        out = torch.empty((walk_count, l), dtype=torch.int32, device=dev)
+    n2v_stored_walk(graph.handle, table.buf, starts, n_starts, r, l, seed, walk_begin, walk_count, out, stream)
+    return out
 
 
 def traffic(graph: Graph, starts, walk_begin: int, walks: torch.Tensor, stream=None) -> tuple[int, int]:

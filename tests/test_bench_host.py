@@ -1,0 +1,40 @@
+"""Host-side logic of bench.py, no GPU: picking the timed launches out of an ncu launch list."""
+import csv
+import json
+
+import bench
+
+
+def write_launch_list(path, kernels):
+    with open(path, "w", newline="") as f:
+        f.write("==PROF== Connected to process 1\n")
+        w = csv.writer(f)
+        w.writerow(["ID", "Kernel Name", "Metric Name", "Metric Unit", "Metric Value"])
+        for i, (name, ns, rd, wr) in enumerate(kernels):
+            w.writerow([i, name, "gpu__time_duration.sum", "ns", f"{ns:,}"])
+            w.writerow([i, name, "dram__bytes_read.sum", "byte", f"{rd:,}"])
+            w.writerow([i, name, "dram__bytes_write.sum", "byte", f"{wr:,}"])
+
+
+def test_ingest_picks_the_timed_launches(tmp_path):
+    K = "void n2v::k_persistent<5>(n2v::GraphView, ...)"
+    npq, warmup, steps = 3, 3, 1
+    launches = [(K, 10, 1, 1)] * 4  # autotuner
+    launches += [("n2v::k_validate_stats", 5, 0, 0)]
+    launches += [(K, 100 + i, 7, 1) for i in range(warmup * npq)]  # warm-up
+    launches += [(K, 200 + i, 1000 * (i + 1), 10 * (i + 1)) for i in range(steps * npq)]  # timed
+    launches += [("at::fill", 1, 0, 0)]
+    launches += [(K, 50, 3, 3)] * (2 * npq)  # comparison: untimed + timed per job
+    launches += [("n2v::k_plain_step", 9, 0, 0)] * 20
+    write_launch_list(tmp_path / "l.csv", launches)
+    line = {"steps": steps, "warmup": warmup,
+            "config": {"pq": [[1, 1], [0.25, 4], [4, 0.25]], "workload": "testwl", "variant": "persistent",
+                       "tune": {"blocks_per_sm": 5}, "walks_per_gpu": 64},
+            "roofline": {"kernel": "k_persistent", "algorithmic_bytes_per_launch": [1, 2, 3]}}
+    (tmp_path / "b.json").write_text("some log line\n" + json.dumps(line) + "\n")
+    p = bench.ingest_ncu(str(tmp_path / "l.csv"), str(tmp_path / "b.json"), str(tmp_path))
+    d = json.load(open(p))
+    assert [x["dram_read"] for x in d["per_launch"]] == [1000, 2000, 3000]
+    assert [x["dram_write"] for x in d["per_launch"]] == [10, 20, 30]
+    assert d["dram_bytes_per_launch"] == (1010 + 2020 + 3030) // 3
+    assert d["tune"] == {"blocks_per_sm": 5} and d["csrc_sha"] == bench.csrc_digest()

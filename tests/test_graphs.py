@@ -73,3 +73,21 @@ def test_uniform_streams():
 def test_from_edges_rejects_conflicts():
     with pytest.raises(ValueError):
         G.from_edges(3, [(0, 1), (1, 0)], weights=[1, 2])
+
+
+def test_skew_and_wec_parameters():
+    """Skew-S (Section 5.1): b = c = 0.25 and d = S a; WeC-K is (.18, .25, .25, .32)."""
+    for S in (1, 2, 3, 4, 5):
+        a, b, c = G.skew_abc(S)
+        d = 1.0 - a - b - c
+        assert b == c == 0.25 and abs(d - S * a) < 1e-12
+        w = G.WORKLOADS[f"skew{S}"]
+        assert w.graph["scale"] == 22 and w.r == 1 and w.l == 80 and w.pq == [(0.5, 2.0)]
+    assert G.SWEEPS["skew"] == [f"skew{S}" for S in (1, 2, 3, 4, 5)]
+    for K in G.SWEEPS["wec"]:
+        a, b, c = G.WORKLOADS[K].graph["abc"]
+        assert (a, b, c) == (0.18, 0.25, 0.25) and abs(1 - a - b - c - 0.32) < 1e-12
+    # more skew puts more of the edges on fewer vertices
+    lo = G.make_graph(dict(kind="rmat", scale=12, ef=50, seed=1, abc=G.skew_abc(1)))
+    hi = G.make_graph(dict(kind="rmat", scale=12, ef=50, seed=1, abc=G.skew_abc(5)))
+    assert hi.degrees().max() > 4 * lo.degrees().max()
