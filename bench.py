@@ -313,9 +313,14 @@ def run_ours(args):
     tuned = None
     if args.autotune and args.variant == "persistent":
         t0 = time.perf_counter()
-        # a sample that fills every resident warp many times over: 2^20 walks of 20 steps
-        best, ms = n2v.autotune(graph, np.arange(g.n, dtype=np.int32), min(wl.l, 20), pq[0][0], pq[0][1], wl.seed,
-                                sample=min(1 << 20, g.n), stream=stream)
+        # the job's first walks (walk id i starts at vertex i mod n): the whole job when it
+        # has at most 2^20 walks, else 2^20 walks of 20 steps, which fill every resident warp
+        # many times over
+        n_job = g.n * wl.r
+        n_tune = min(1 << 20, n_job)
+        tune_starts = np.resize(np.arange(g.n, dtype=np.int32), n_tune)
+        best, ms = n2v.autotune(graph, tune_starts, wl.l if n_tune == n_job else min(wl.l, 20), pq[0][0], pq[0][1],
+                                wl.seed, sample=n_tune, stream=stream)
         tuned = {"tune": best.as_dict(), "sample_ms": round(ms, 3), "tune_s": round(time.perf_counter() - t0, 2)}
         tune = best
     info = graph.info()
