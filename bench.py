@@ -82,9 +82,9 @@ def dist_env():
 
 
 # the sources the sampler kernels are compiled from (the autotuner, serving
-# loop and graph loader are not part of them)
+# loop, graph loader and the header's documentation are not part of them)
 KERNEL_SOURCES = ["paper_1805_00280_gb300/csrc/n2v_walk.cu", "paper_1805_00280_gb300/csrc/n2v_step.cuh",
-                  "paper_1805_00280_gb300/csrc/n2v_internal.cuh", "include/n2v.h"]
+                  "paper_1805_00280_gb300/csrc/n2v_internal.cuh"]
 
 
 def csrc_digest() -> str:
@@ -175,6 +175,13 @@ def ncu_traffic(workload: str, variant: str, tune: dict):
 
 # --------------------------------------------------------------------------
 # CPU baseline: the oracle, as it stands, on a bounded sample of walk ids
+
+def oracle_mod():
+    """The CPU oracle (test infrastructure; only the CPU-baseline and parity legs use it)."""
+    import oracle
+
+    return oracle
+
 
 def cpu_oracle_sample(g, starts_np, r, l, pq, seed, budget_s, threads, id_space, rng_seed=0, check=None):
     import numpy as np
@@ -380,11 +387,12 @@ def run_ours(args):
         raise RuntimeError(f"sampler status {n2v.n2v_strerror(st)}")
 
     # ---- work done per step (deterministic rows, so the same every step)
-    trans, abytes = [], []
+    trans, abytes, lbytes = [], [], []
     for i in range(len(pq)):
-        tr, by = n2v.traffic(graph, starts, walk_begin, outs[i])
+        tr, by, lo = n2v.traffic(graph, starts, walk_begin, outs[i])
         trans.append(tr)
         abytes.append(by)
+        lbytes.append(lo)
     steps_per_step = sum(trans) * world  # all ranks
     value = steps_per_step * args.steps / (total_ms / 1e3)
     mean_launch_ms = [statistics.mean(launch_ms[s][i] for s in range(args.steps)) for i in range(len(pq))]
@@ -398,6 +406,12 @@ def run_ours(args):
                 "algorithmic_bytes_per_launch": [int(b) for b in abytes],
                 "kernel": {"persistent": "k_persistent", "binned": "k_binned_step", "plain": "k_plain_step"}[args.variant],
                 "bytes_model": "16 + 4 deg(v) (1+weighted) + [k>=1](16 + 4 deg(t)) + 4 per real transition"}
+    # the conservative lower model: N(v) and the output only, no N(t) message
+    lower_achieved = sum(lbytes) / (sum(mean_launch_ms) / 1e3) / 1e9
+    roofline["lower_model"] = {"bytes_model": "16 + 4 deg(v) (1+weighted) + 4 per real transition",
+                               "algorithmic_bytes_per_launch": [int(b) for b in lbytes],
+                               "achieved": lower_achieved, "frac": lower_achieved / peak}
+    step_ms = [sum(row) for row in launch_ms]
 
     # ---- the other variants, once each on the first rounds of walk ids (every start vertex
     #      `compare_rounds` times), beside the main variant on the same rows
@@ -409,7 +423,7 @@ def run_ours(args):
         sub = {}
         for vname in [args.variant] + names:
             vcode = n2v.VARIANTS[vname]
-            ms, same, tr = [], True, 0
+            ms, same, tr, shas = [], True, 0, []
             for i in range(len(pq)):
                 launch_sub = lambda: n2v.n2v_walk(graph.handle, starts, n_start, r_total, l, pq[i][0], pq[i][1],
                                                   wl.seed, walk_begin, Wc, tmp, ws, vcode, stream)
@@ -424,8 +438,9 @@ def run_ours(args):
                 ms.append(a.elapsed_time(b))
                 same &= bool(torch.equal(tmp, outs[i][:Wc]))
                 tr += n2v.traffic(graph, starts, walk_begin, tmp)[0]
+                shas.append(hashlib.sha256(tmp.cpu().numpy()).hexdigest())
             sub[vname] = {"value": tr * world / (sum(ms) / 1e3), "unit": UNIT, "ms": sum(ms),
-                          "bit_identical_to_timed_" + args.variant: same,
+                          "bit_identical_to_timed_" + args.variant: same, "rows_sha256": shas,
                           "launches": len(pq) * (l if vname != "persistent" else 1)}
         del tmp
         compare = {"walks_per_pq": Wc, "variants": sub}
@@ -464,6 +479,12 @@ def run_ours(args):
         e2e = {"value": steps_per_step * K2 / (e2e_ms / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": 4 * n_start * len(pq), "d2h_bytes_per_step": 4 * W * l * len(pq),
                "steps": K2, "path": "pinned host starts -> n2v_walk -> pinned host walks, per (p,q)"}
+        # SHA-256 of every (p,q) job's full output, through the same host buffer (after the timing)
+        out_sha = []
+        for i in range(len(pq)):
+            out_h.copy_(outs[i])
+            out_sha.append(hashlib.sha256(out_h.numpy()).hexdigest())
+        e2e["output_sha256"] = out_sha
         del out_h
 
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only)
@@ -483,11 +504,34 @@ def run_ours(args):
                                                           W, check=check)
         cpu = {"value": steps_c / t_c, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": f"random walk-id samples of sizes {desc} per (p,q) out of {W}"}
-        parity = {"oracle_rows_checked": nrows, "bit_exact": ok}
+        # the same oracle on one core, on a small sample of the first job
+        ids1 = np.sort(np.random.default_rng(2).choice(W, size=min(256, W), replace=False))
+        t0 = time.perf_counter()
+        rows1 = oracle_mod().walk(g.row_ptr, g.col, g.w, starts_np, l, pq[0][0], pq[0][1], wl.seed, ids1, threads=1)
+        cpu["one_core"] = {"value": int((rows1 >= 0).sum()) / (time.perf_counter() - t0), "unit": UNIT,
+                           "sample": f"{len(ids1)} random walk ids of the first (p,q)"}
+        ok &= check(pq[0][0], pq[0][1], ids1, rows1)
+        # parity beyond the timed sample: at least 2^14 random walk ids in all, and every walk
+        # that starts at one of the 100 highest-degree vertices
+        n_rand = sum(desc)
+        extra = np.sort(np.random.default_rng(3).choice(W, size=min(max(0, (1 << 14) - n_rand), W), replace=False))
+        hubs = np.sort(np.argsort(g.degrees(), kind="stable")[-100:])
+        hub_ids = np.array([k * n_start + h for k in range(W // n_start) for h in hubs], dtype=np.int64)
+        hub_ids = hub_ids[hub_ids < W]
+        for ids_x in (extra, hub_ids):
+            if ids_x.size == 0:
+                continue
+            for (p, q) in pq:
+                rows_x = oracle_mod().walk(g.row_ptr, g.col, g.w, starts_np, l, p, q, wl.seed, ids_x, threads=threads)
+                ok &= check(p, q, ids_x, rows_x)
+                nrows += len(ids_x)
+        parity = {"oracle_rows_checked": nrows + len(ids1), "random_walk_ids": n_rand + int(extra.size),
+                  "hub_start_walk_ids": int(hub_ids.size), "hub_vertices": int(hubs.size), "bit_exact": ok}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "ms_per_step_median": statistics.median(step_ms),
+        "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": wl.name, "desc": wl.note, "n": g.n, "nnz": g.nnz, "weighted": g.w is not None,
                    "r": r, "l": l, "pq": pq, "walks_per_gpu": W, "variant": args.variant,

@@ -218,11 +218,12 @@ int n2v_alpha_q16(double p, double q, uint32_t* a_p, uint32_t* a_q);
 /* Count, over walk rows [walk_begin, walk_begin + walk_count) that n2v_walk
  * wrote to `walks`, the real transitions (entries != -1) and the adjacency
  * bytes of the per-step model of Section 3.2 (N(v) read locally, N(t) as the
- * NEIG message): 16 + 4*deg(v)*(1 + weighted) + [k >= 1]*(16 + 4*deg(t)) + 4.
- * out2 is DEVICE uint64[2] and is overwritten: out2[0] = transitions,
- * out2[1] = bytes.  Asynchronous on `stream`. */
+ * NEIG message): 16 + 4*deg(v)*(1 + weighted) + [k >= 1]*(16 + 4*deg(t)) + 4,
+ * and of the lower model without the N(t) term: 16 + 4*deg(v)*(1 + weighted) + 4.
+ * out3 is DEVICE uint64[3] and is overwritten: out3[0] = transitions,
+ * out3[1] = model bytes, out3[2] = lower-model bytes.  Asynchronous on `stream`. */
 int n2v_walk_traffic(const n2v_graph* g, const int32_t* starts, int64_t n_starts, int64_t walk_begin,
-                     int64_t walk_count, int32_t l, const int32_t* walks, uint64_t* out2, void* stream);
+                     int64_t walk_count, int32_t l, const int32_t* walks, uint64_t* out3, void* stream);
 
 /* Synchronise `stream`, return and clear the device status word of `g`
  * (N2V_OK, N2V_ERR_INVALID_ARG or N2V_ERR_TIMEOUT), or N2V_ERR_CUDA when the

@@ -147,17 +147,17 @@ def walk(row_ptr, col, w, starts, l: int, p: float, q: float, seed: int, walk_id
     return out
 
 
-def traffic(row_ptr, weighted: bool, starts, walk_ids, walks) -> tuple[int, int]:
-    """(real transitions, model adjacency bytes) over the given rows."""
+def traffic(row_ptr, weighted: bool, starts, walk_ids, walks) -> tuple[int, int, int]:
+    """(real transitions, model adjacency bytes, lower-model bytes) over the given rows."""
     row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
     starts = np.ascontiguousarray(starts, dtype=np.int32)
     ids = np.ascontiguousarray(walk_ids, dtype=np.int64)
     walks = np.ascontiguousarray(walks, dtype=np.int32)
-    out = np.zeros(2, dtype=np.uint64)
+    out = np.zeros(3, dtype=np.uint64)
     lib().n2v_oracle_traffic(row_ptr.ctypes.data, int(weighted), starts.ctypes.data, starts.shape[0],
                              ids.ctypes.data, ids.shape[0], walks.ctypes.data, walks.shape[1],
                              out.ctypes.data)
-    return int(out[0]), int(out[1])
+    return int(out[0]), int(out[1]), int(out[2])
 
 
 def approx_decide(deg_v: int, deg_t: int, a_p: int, a_q: int, w_min: int, w_max: int,

@@ -153,8 +153,8 @@ void n2v_oracle_walk(const int64_t* row_ptr, const int32_t* col, const uint32_t*
 
 void n2v_oracle_traffic(const int64_t* row_ptr, int weighted, const int32_t* starts, int64_t n_starts,
                         const int64_t* walk_ids, int64_t n_ids, const int32_t* walks, int32_t l,
-                        uint64_t out[2]) {
-  uint64_t steps = 0, bytes = 0;
+                        uint64_t out[3]) {
+  uint64_t steps = 0, bytes = 0, lower = 0;
   for (int64_t i = 0; i < n_ids; ++i) {
     const int32_t* row = walks + i * (int64_t)l;
     int64_t s0 = starts[(uint64_t)walk_ids[i] % (uint64_t)n_starts];
@@ -162,8 +162,9 @@ void n2v_oracle_traffic(const int64_t* row_ptr, int weighted, const int32_t* sta
       if (row[k] < 0) break;
       int64_t v = (k == 0) ? s0 : row[k - 1];
       uint64_t dv = (uint64_t)(row_ptr[v + 1] - row_ptr[v]);
-      uint64_t b = 16 + 4 * dv * (weighted ? 2 : 1) + 4;
-      if (k >= 1) {
+      uint64_t b = 16 + 4 * dv * (weighted ? 2 : 1) + 4; /* N(v) read locally, output */
+      lower += b;
+      if (k >= 1) { /* N(t) as the NEIG message */
         int64_t t = (k == 1) ? s0 : row[k - 2];
         b += 16 + 4 * (uint64_t)(row_ptr[t + 1] - row_ptr[t]);
       }
@@ -173,6 +174,7 @@ void n2v_oracle_traffic(const int64_t* row_ptr, int weighted, const int32_t* sta
   }
   out[0] = steps;
   out[1] = bytes;
+  out[2] = lower;
 }
 
 /* ---------------------------------------------------------------------- */

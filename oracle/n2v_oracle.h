@@ -74,10 +74,12 @@ void n2v_oracle_walk_approx(const int64_t* row_ptr, const int32_t* col, const ui
 
 /* Counts of the given walk rows: out[0] = real transitions (entries != -1),
  * out[1] = adjacency bytes by the per-step model
- *   16 + 4*deg(v)*(1 + weighted) + [k >= 1] * (16 + 4*deg(t)) + 4. */
+ *   16 + 4*deg(v)*(1 + weighted) + [k >= 1] * (16 + 4*deg(t)) + 4,
+ * out[2] = bytes by the lower model without the N(t) term,
+ *   16 + 4*deg(v)*(1 + weighted) + 4. */
 void n2v_oracle_traffic(const int64_t* row_ptr, int weighted, const int32_t* starts, int64_t n_starts,
                         const int64_t* walk_ids, int64_t n_ids, const int32_t* walks, int32_t l,
-                        uint64_t out[2]);
+                        uint64_t out[3]);
 
 #ifdef __cplusplus
 }

@@ -147,8 +147,8 @@ __global__ void __launch_bounds__(kPersistThreads, MINB)
 // Traffic counter: one thread per row.
 __global__ void k_traffic(const int64_t* __restrict__ rp, int weighted, const int32_t* __restrict__ starts,
                           int64_t n_starts, int64_t walk_begin, int64_t count, int32_t l,
-                          const int32_t* __restrict__ walks, unsigned long long* __restrict__ out2) {
-  unsigned long long steps = 0, bytes = 0;
+                          const int32_t* __restrict__ walks, unsigned long long* __restrict__ out3) {
+  unsigned long long steps = 0, bytes = 0, lower = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t* row = walks + i * (int64_t)l;
     const int64_t s0 = starts[(walk_begin + i) % n_starts];
@@ -156,10 +156,10 @@ __global__ void k_traffic(const int64_t* __restrict__ rp, int weighted, const in
     for (int k = 0; k < l; ++k) {
       const int32_t x = row[k];
       if (x < 0 || v < 0) break;
-      unsigned long long b = 16 + 4ull * (unsigned long long)(rp[v + 1] - rp[v]) * (weighted ? 2 : 1) + 4;
-      if (k >= 1) b += 16 + 4ull * (unsigned long long)(rp[t + 1] - rp[t]);
+      const unsigned long long b = 16 + 4ull * (unsigned long long)(rp[v + 1] - rp[v]) * (weighted ? 2 : 1) + 4;
       steps += 1;
-      bytes += b;
+      lower += b;
+      bytes += b + (k >= 1 ? 16 + 4ull * (unsigned long long)(rp[t + 1] - rp[t]) : 0ull);
       t = v;
       v = x;
     }
@@ -167,10 +167,12 @@ __global__ void k_traffic(const int64_t* __restrict__ rp, int weighted, const in
   for (int o = 16; o > 0; o >>= 1) {
     steps += __shfl_xor_sync(kFull, steps, o);
     bytes += __shfl_xor_sync(kFull, bytes, o);
+    lower += __shfl_xor_sync(kFull, lower, o);
   }
   if ((threadIdx.x & 31) == 0 && (steps || bytes)) {
-    atomicAdd(&out2[0], steps);
-    atomicAdd(&out2[1], bytes);
+    atomicAdd(&out3[0], steps);
+    atomicAdd(&out3[1], bytes);
+    atomicAdd(&out3[2], lower);
   }
 }
 
@@ -479,15 +481,15 @@ static int walk_impl(const n2v_graph* g, const int32_t* starts, int64_t n_starts
 }
 
 int n2v_walk_traffic(const n2v_graph* g, const int32_t* starts, int64_t n_starts, int64_t walk_begin,
-                     int64_t walk_count, int32_t l, const int32_t* walks, uint64_t* out2, void* stream) {
-  if (!g || !out2 || l < 1 || n_starts < 1 || walk_begin < 0 || walk_count < 0) return N2V_ERR_INVALID_ARG;
+                     int64_t walk_count, int32_t l, const int32_t* walks, uint64_t* out3, void* stream) {
+  if (!g || !out3 || l < 1 || n_starts < 1 || walk_begin < 0 || walk_count < 0) return N2V_ERR_INVALID_ARG;
   if (walk_count > 0 && (!starts || !walks)) return N2V_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
-  if (cudaMemsetAsync(out2, 0, 2 * sizeof(uint64_t), s) != cudaSuccess) return N2V_ERR_CUDA;
+  if (cudaMemsetAsync(out3, 0, 3 * sizeof(uint64_t), s) != cudaSuccess) return N2V_ERR_CUDA;
   if (walk_count == 0) return N2V_OK;
   const unsigned blocks = (unsigned)std::min<int64_t>((walk_count + 255) / 256, (int64_t)g->sms * 16);
   k_traffic<<<blocks, 256, 0, s>>>(g->view.rp, g->weighted, starts, n_starts, walk_begin, walk_count, l, walks,
-                                   (unsigned long long*)out2);
+                                   (unsigned long long*)out3);
   return cudaGetLastError() == cudaSuccess ? N2V_OK : N2V_ERR_CUDA;
 }
 

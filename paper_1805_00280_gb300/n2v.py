@@ -463,15 +463,15 @@ def stored_walk(graph: Graph, table: StoredTable, starts, r: int, l: int, seed: 
     return out
 
 
-def traffic(graph: Graph, starts, walk_begin: int, walks: torch.Tensor, stream=None) -> tuple[int, int]:
-    """(real transitions, model adjacency bytes) of the rows in ``walks`` (synchronises)."""
+def traffic(graph: Graph, starts, walk_begin: int, walks: torch.Tensor, stream=None) -> tuple[int, int, int]:
+    """(real transitions, model adjacency bytes, lower-model bytes) of the rows in ``walks`` (synchronises)."""
     dev = graph.row_ptr.device
     starts = torch.as_tensor(starts, dtype=torch.int32).to(dev).contiguous()
-    out2 = torch.zeros(2, dtype=torch.int64, device=dev)
+    out3 = torch.zeros(3, dtype=torch.int64, device=dev)
     n2v_walk_traffic(graph.handle, starts, int(starts.numel()), walk_begin, int(walks.shape[0]),
-                     int(walks.shape[1]), walks, out2, stream)
-    o = out2.cpu()
-    return int(o[0]), int(o[1])
+                     int(walks.shape[1]), walks, out3, stream)
+    o = out3.cpu()
+    return int(o[0]), int(o[1]), int(o[2])
 
 
 class Server:

@@ -129,6 +129,16 @@ def test_er_traffic_matches_oracle(er):
                                                                   np.arange(want.shape[0]), want)
 
 
+def test_weighted_traffic_matches_oracle():
+    g = G.with_weights(G.rmat(12, 16, 0.57, 0.19, 0.19, 8), 3, 1, 100)
+    graph = n2v.Graph.from_csr(g)
+    starts = np.arange(g.n, dtype=np.int32)
+    walks = n2v.walk(graph, starts, 3, 30, 0.5, 2.0, 5, "persistent")
+    got = n2v.traffic(graph, starts, 0, walks)
+    want = oracle.traffic(g.row_ptr, True, starts, np.arange(walks.shape[0]), walks.cpu().numpy())
+    assert got == want and got[2] < got[1]
+
+
 def test_split_ranges_equal_whole(er):
     """Any split of the walk-id range (chunking, sharding) gives the same rows."""
     g, starts, wl, want = er

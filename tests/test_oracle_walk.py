@@ -346,7 +346,7 @@ def test_traffic_model_counts():
     ids = np.arange(6)
     rows = run(g, starts, 5, 0.5, 2.0, 4, ids)
     deg = g.degrees()
-    steps = bytes_ = 0
+    steps = bytes_ = lower = 0
     for i, wid in enumerate(ids):
         s0 = int(starts[wid % 2])
         for k in range(5):
@@ -354,9 +354,10 @@ def test_traffic_model_counts():
                 break
             v = s0 if k == 0 else int(rows[i, k - 1])
             b = 16 + 8 * int(deg[v]) + 4
+            lower += b
             if k >= 1:
                 t = s0 if k == 1 else int(rows[i, k - 2])
                 b += 16 + 4 * int(deg[t])
             steps += 1
             bytes_ += b
-    assert oracle.traffic(g.row_ptr, True, starts, ids, rows) == (steps, bytes_)
+    assert oracle.traffic(g.row_ptr, True, starts, ids, rows) == (steps, bytes_, lower)
