@@ -306,7 +306,7 @@ int n2v_serve_stats(n2v_server* s, n2v_serve_stats_t* st);
 /* Destroy the server (synchronise the stream first; the arena stays the caller's). */
 void n2v_serve_destroy(n2v_server* s);
 
-/* Failure-path self-test (SURVEY's failure detection, no paper counterpart):
+/* Failure-path self-test (failure detection without a GPU fault; the paper has no counterpart):
  * launch one warp that waits on an mbarrier nothing arrives on, with the
  * samplers' bounded wait and a limit of limit_cycles SM cycles (1 .. 2^34).
  * It gives up, records N2V_ERR_TIMEOUT in the status word of g and returns;

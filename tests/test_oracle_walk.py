@@ -122,7 +122,7 @@ def test_enumeration_chi2(name, s0, pq):
     dist_q16 = path_distribution(g, s0, l, a_p, 65536, a_q)
     assert sum(dist_q16.values()) == 1
     assert chi2_pvalue(rows, dist_q16) > 1e-3
-    # the real-valued alpha gives the same verdict: Q16 rounding is below 2^-17 relative
+    # the real-valued alpha gives the same outcome: Q16 rounding is below 2^-17 relative
     dist_real = path_distribution(g, s0, l, 1 / Fraction(p), Fraction(1), 1 / Fraction(q))
     assert chi2_pvalue(rows, dist_real) > 1e-3
 
