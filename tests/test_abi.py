@@ -84,3 +84,34 @@ def test_host_argument_checks_need_no_gpu():
     b = ctypes.c_size_t()
     assert L.n2v_walk_ws_bytes(None, 1, 1, 0, ctypes.byref(b)) == n2v.N2V_ERR_INVALID_ARG
     L.n2v_graph_free(None)  # no-op
+
+
+@pytest.mark.parametrize("field,value", [("block_threads", 512), ("block_threads", 48), ("block_threads", 32),
+                                         ("stage_window", 100), ("stage_window", 8192), ("stage_buffers", 3),
+                                         ("smem_specials", 48), ("smem_specials", 16), ("stream_ratio", -1),
+                                         ("blocks_per_sm", -1), ("hub_budget_mb", -1)])
+def test_tune_validation_rejects(field, value):
+    t = n2v.n2v_tune_default()
+    setattr(t, field, value)
+    with pytest.raises(n2v.N2VError):
+        n2v.n2v_graph_aux_bytes(1000, 10_000, False, t)
+
+
+@pytest.mark.parametrize("field,value", [("block_threads", 64), ("block_threads", 256), ("stage_window", 0),
+                                         ("stage_window", 4096), ("stage_buffers", 4), ("blocks_per_sm", 8)])
+def test_tune_validation_accepts(field, value):
+    t = n2v.n2v_tune_default()
+    setattr(t, field, value)
+    assert n2v.n2v_graph_aux_bytes(1000, 10_000, False, t) > 0
+
+
+def test_stored_serve_and_tuner_host_checks_need_no_gpu():
+    L = n2v.lib()
+    b, e = ctypes.c_size_t(), ctypes.c_int64()
+    assert L.n2v_stored_bytes(None, None, ctypes.byref(b), ctypes.byref(e)) == n2v.N2V_ERR_INVALID_ARG
+    assert L.n2v_stored_build(None, 1.0, 1.0, None, 0, None) == n2v.N2V_ERR_INVALID_ARG
+    assert L.n2v_stored_walk(None, None, None, 1, 1, 1, 1, 0, 1, None, None) == n2v.N2V_ERR_INVALID_ARG
+    srv = ctypes.c_void_p()
+    assert L.n2v_serve_create(None, None, 0, None, None, ctypes.byref(srv)) == n2v.N2V_ERR_INVALID_ARG
+    assert L.n2v_autotune_ws_bytes(None, 1, 1, ctypes.byref(b)) == n2v.N2V_ERR_INVALID_ARG
+    assert L.n2v_walk_traffic(None, None, 1, 0, 0, 1, None, None, None) == n2v.N2V_ERR_INVALID_ARG
