@@ -10,7 +10,7 @@ A "step" of this benchmark is one pass of the whole hot path over one batch:
 every walk of the workload (r walks from every vertex, length l) for every
 (p, q) setting of the workload, on a resident graph, through the C ABI.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload rmat20]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload rmat26]
     python bench.py --impl reference ...   # the CPU oracle on the host cores
 
 Under torchrun (N > 1) every rank runs the same per-GPU workload on its own
@@ -41,7 +41,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="rmat20")
+    ap.add_argument("--workload", default="rmat26")
     ap.add_argument("--variant", default="persistent", choices=["persistent", "binned", "plain"])
     ap.add_argument("--compare", default="plain,binned,stored",
                     help="variants timed once beside the main one (stored: the stored-table baseline)")
@@ -55,7 +55,10 @@ def parse_args():
     ap.add_argument("--walk-count", type=int, default=0, help="limit walks per launch (profiling cases)")
     ap.add_argument("--compare-rounds", type=int, default=1,
                     help="the compared variants run the first R rounds (every start vertex R times)")
-    ap.add_argument("--compare-walks", type=int, default=1 << 22, help="cap on the walks of the compared variants")
+    ap.add_argument("--compare-walks", type=int, default=0,
+                    help="cap on the walks of the compared variants (0: the workload's default)")
+    ap.add_argument("--c2", type=int, default=-1,
+                    help="add the R-MAT 20 persistent / binned / plain block (-1: per workload)")
     ap.add_argument("--sweep", default="", help="run every workload of a sweep (skew, wec), one JSON line each")
     ap.add_argument("--ingest-ncu", nargs=2, metavar=("LAUNCH_CSV", "BENCH_JSON"), default=None,
                     help="write profiles/traffic_<variant>_<workload>.json from an ncu launch list (with DRAM bytes) "
@@ -68,9 +71,13 @@ def parse_args():
 
 
 # workload-specific defaults: the scale-26 graph runs in 8M-walker launches
-# (FN-Multi-style rounds) recorded as one CUDA graph
+# (FN-Multi-style rounds) recorded as one CUDA graph; its compared variants run
+# 2^20 walks in four ranges spread over the job, and the line carries the
+# R-MAT 20 persistent / binned / plain block
 WORKLOAD_DEFAULTS = {
-    "rmat26": {"tune": {"chunk_walkers": 1 << 23}, "cuda_graph": 1},
+    "rmat26": {"tune": {"chunk_walkers": 1 << 23}, "cuda_graph": 1, "compare_walks": 1 << 20, "compare_ranges": 4,
+               "c2": 1},
+    "rmat22": {"cuda_graph": 1},
 }
 
 
@@ -413,43 +420,20 @@ def run_ours(args):
                                "achieved": lower_achieved, "frac": lower_achieved / peak}
     step_ms = [sum(row) for row in launch_ms]
 
-    # ---- the other variants, once each on the first rounds of walk ids (every start vertex
-    #      `compare_rounds` times), beside the main variant on the same rows
+    # ---- the other variants, once each, beside the main variant on the same rows: the first
+    #      `compare_rounds` rounds of walk ids, or (large jobs) contiguous id ranges spread
+    #      evenly over the job
     compare = {}
-    Wc = min(W, n_start * max(1, args.compare_rounds), args.compare_walks)
+    ranges = compare_ranges(W, n_start, args, wdef)
     names = [v for v in args.compare.split(",") if v and v != args.variant and v != "stored"]
     if names:
-        tmp = torch.empty((Wc, l), dtype=torch.int32, device=dev)
-        sub = {}
-        for vname in [args.variant] + names:
-            vcode = n2v.VARIANTS[vname]
-            ms, same, tr, shas = [], True, 0, []
-            for i in range(len(pq)):
-                launch_sub = lambda: n2v.n2v_walk(graph.handle, starts, n_start, r_total, l, pq[i][0], pq[i][1],
-                                                  wl.seed, walk_begin, Wc, tmp, ws, vcode, stream)
-                launch_sub()  # warm-up
-                torch.cuda.synchronize(dev)
-                flush.fill_(7)
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                launch_sub()
-                b.record(stream)
-                torch.cuda.synchronize(dev)
-                ms.append(a.elapsed_time(b))
-                same &= bool(torch.equal(tmp, outs[i][:Wc]))
-                tr += n2v.traffic(graph, starts, walk_begin, tmp)[0]
-                shas.append(hashlib.sha256(tmp.cpu().numpy()).hexdigest())
-            sub[vname] = {"value": tr * world / (sum(ms) / 1e3), "unit": UNIT, "ms": sum(ms),
-                          "bit_identical_to_timed_" + args.variant: same, "rows_sha256": shas,
-                          "launches": len(pq) * (l if vname != "persistent" else 1)}
-        del tmp
-        compare = {"walks_per_pq": Wc, "variants": sub}
-        if "plain" in sub:
-            compare["speedup_over_plain_same_rows"] = sub[args.variant]["value"] / sub["plain"]["value"]
+        compare = compare_variants(n2v, graph, starts, n_start, r_total, l, pq, wl.seed, walk_begin, ranges,
+                                   [args.variant] + names, outs, ws, stream, dev, world, flush, args.variant)
     if "stored" in args.compare.split(","):
-        compare.setdefault("walks_per_pq", Wc)
-        compare["stored"] = stored_compare(n2v, graph, g, starts, n_start, r_total, l, pq, wl.seed, walk_begin, Wc,
-                                           outs, stream, dev, world, flush)
+        Wc = ranges[0][1]  # the first range starts at walk id offset 0
+        compare["stored"] = stored_compare(n2v, graph, g, starts, n_start, r_total, l, pq, wl.seed, walk_begin,
+                                           Wc, outs, stream, dev, world, flush)
+        compare["stored"]["walks_per_pq"] = Wc
 
     # ---- end to end through the C ABI with host buffers
     e2e = None
@@ -528,6 +512,12 @@ def run_ours(args):
         parity = {"oracle_rows_checked": nrows + len(ids1), "random_walk_ids": n_rand + int(extra.size),
                   "hub_start_walk_ids": int(hub_ids.size), "hub_vertices": int(hubs.size), "bit_exact": ok}
 
+    # ---- the R-MAT 20 workload's three samplers on the same rows (single-GPU runs)
+    c2 = None
+    use_c2 = bool(wdef.get("c2", 0)) if args.c2 < 0 else bool(args.c2)
+    if use_c2 and world == 1 and args.variant == "persistent":
+        c2 = c2_block(n2v, dev, stream, flush, check_oracle=not args.no_cpu)
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "ms_per_step_median": statistics.median(step_ms),
@@ -550,6 +540,7 @@ def run_ours(args):
             (-(-W // tune.chunk_walkers) if tune.chunk_walkers > 0 else 1) if args.variant == "persistent" else l),
         "clocks": clk,
         "compare": compare,
+        "c2": c2,
         "parity": parity,
         "wall_s_timed": wall,
     }
@@ -722,6 +713,110 @@ def degree_bins(graph, info, rows) -> dict:
     vs = [int(x) for x in info.deg_hist]
     last = max([i for i in range(34) if vs[i]] + [0]) + 1
     return {"vertices": vs[:last], "visits": [int(x) for x in visits.cpu()][:last]}
+
+
+def compare_ranges(W: int, n_start: int, args, wdef: dict) -> list[tuple[int, int]]:
+    """Walk-id ranges (offset, count) inside this rank's W walks on which the compared variants run.
+
+    Small jobs: the first `compare_rounds` rounds (every start vertex that many times), capped by
+    `compare_walks`.  Jobs with a per-workload `compare_ranges` default: that many contiguous
+    ranges of compare_walks / ranges walks each, at evenly spaced offsets over the job, so that
+    both the low-numbered hubs of an R-MAT graph and its sparse tail are sampled."""
+    k = int(wdef.get("compare_ranges", 1))
+    total = min(W, args.compare_walks if args.compare_walks > 0 else int(wdef.get("compare_walks", 1 << 22)))
+    if k <= 1:
+        return [(0, min(total, n_start * max(1, args.compare_rounds)))]
+    each = max(1, total // k)
+    return [(min(i * (W // k), W - each), each) for i in range(k)]
+
+
+def compare_variants(n2v, graph, starts, n_start, r_total, l, pq, seed, walk_begin, ranges, variants, outs, ws,
+                     stream, dev, world, flush, main_variant):
+    """Each variant once (after an untimed run on a small range) on the same walk-id ranges; the
+    rows are compared with the timed main variant's output."""
+    import torch
+
+    cnt = max(c for _, c in ranges)
+    tmp = torch.empty((cnt, l), dtype=torch.int32, device=dev)
+    sub = {}
+    for vname in variants:
+        vcode = n2v.VARIANTS[vname]
+        ms, same, tr, shas = [], True, 0, []
+        for i in range(len(pq)):
+            def call(off, c):
+                n2v.n2v_walk(graph.handle, starts, n_start, r_total, l, pq[i][0], pq[i][1], seed, walk_begin + off,
+                             c, tmp[:c], ws, vcode, stream)
+
+            call(ranges[0][0], min(ranges[0][1], 4096))  # warm-up: module load, function attributes
+            torch.cuda.synchronize(dev)
+            flush.fill_(7)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            h = hashlib.sha256()
+            t_ms = 0.0
+            for off, c in ranges:
+                a.record(stream)
+                call(off, c)
+                b.record(stream)
+                torch.cuda.synchronize(dev)
+                t_ms += a.elapsed_time(b)
+                same &= bool(torch.equal(tmp[:c], outs[i][off:off + c]))
+                tr += n2v.traffic(graph, starts, walk_begin + off, tmp[:c])[0]
+                h.update(tmp[:c].cpu().numpy().tobytes())
+            ms.append(t_ms)
+            shas.append(h.hexdigest())
+        sub[vname] = {"value": tr * world / (sum(ms) / 1e3), "unit": UNIT, "ms": sum(ms),
+                      "bit_identical_to_timed_" + main_variant: same, "rows_sha256": shas,
+                      "launches": len(pq) * len(ranges) * (l if vname != "persistent" else 1)}
+    del tmp
+    res = {"walks_per_pq": sum(c for _, c in ranges), "ranges": ranges, "variants": sub}
+    if "plain" in sub:
+        res["speedup_over_plain_same_rows"] = sub[main_variant]["value"] / sub["plain"]["value"]
+    if "binned" in sub:
+        res["speedup_over_binned_same_rows"] = sub[main_variant]["value"] / sub["binned"]["value"]
+    return res
+
+
+def c2_block(n2v, dev, stream, flush, check_oracle: bool) -> dict:
+    """R-MAT scale 20 (r = 10, l = 80, three (p, q)): the persistent sampler (autotuned) beside the
+    binned and plain samplers on the same rows -- the first round of walk ids, every vertex once --
+    with the rows of all three compared, and sampled rows checked against the oracle."""
+    import numpy as np
+    import torch
+
+    from paper_1805_00280_gb300 import graphs as G
+
+    wl = G.WORKLOADS["rmat20"]
+    g = G.workload_graph("rmat20")
+    graph = n2v.Graph.from_csr(g, device=dev)
+    W = g.n  # the first round: walk ids [0, n)
+    n2v.autotune(graph, np.arange(g.n, dtype=np.int32), 20, wl.pq[0][0], wl.pq[0][1], wl.seed,
+                 sample=min(1 << 20, g.n), stream=stream)
+    starts = torch.arange(g.n, dtype=torch.int32, device=dev)
+    ws_bytes = max(n2v.n2v_walk_ws_bytes(graph.handle, W, wl.l, n2v.N2V_PERSISTENT), 256)
+    ws = torch.empty(ws_bytes // 8 + 32, dtype=torch.int64, device=dev)
+    outs = [torch.empty((W, wl.l), dtype=torch.int32, device=dev) for _ in wl.pq]
+    for i, (p, q) in enumerate(wl.pq):
+        n2v.n2v_walk(graph.handle, starts, g.n, wl.r, wl.l, p, q, wl.seed, 0, W, outs[i], ws, n2v.N2V_PERSISTENT,
+                     stream)
+    torch.cuda.synchronize(dev)
+    res = compare_variants(n2v, graph, starts, g.n, wl.r, wl.l, wl.pq, wl.seed, 0, [(0, W)],
+                           ["persistent", "binned", "plain"], outs, ws, stream, dev, 1, flush, "persistent")
+    res.update({"workload": "rmat20", "desc": wl.note, "n": g.n, "nnz": g.nnz, "pq": wl.pq,
+                "tune": graph.tune.as_dict()})
+    if check_oracle:
+        ok, nrows = True, 0
+        rng = np.random.default_rng(20)
+        hubs = np.sort(np.argsort(g.degrees(), kind="stable")[-64:])
+        ids = np.unique(np.concatenate([rng.choice(W, size=2048, replace=False), hubs]))
+        for i, (p, q) in enumerate(wl.pq):
+            want = oracle_mod().walk(g.row_ptr, g.col, None, np.arange(g.n, dtype=np.int32), wl.l, p, q, wl.seed,
+                                     ids, threads=os.cpu_count() or 1)
+            ok &= bool(np.array_equal(outs[i][torch.from_numpy(ids).to(dev)].cpu().numpy(), want))
+            nrows += len(ids)
+        res["parity"] = {"oracle_rows_checked": nrows, "bit_exact": ok}
+    del outs
+    graph.close()
+    return res
 
 
 def stored_compare(n2v, graph, g, starts, n_start, r_total, l, pq, seed, walk_begin, Wc, outs, stream, dev, world,

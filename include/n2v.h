@@ -192,7 +192,9 @@ int n2v_walk(const n2v_graph* g, const int32_t* starts, int64_t n_starts, int32_
  * capture.  Every call on a device shares the one scratch array: calls that
  * overlap on the GPU (other streams, other threads, other graph handles)
  * race and give wrong rows; serialise them.  The scratch keeps the last
- * call's contents and each call clears what must start at zero.  Returns
+ * call's contents and each call clears what must start at zero.  The
+ * device current at the call must be the one the graph was loaded on (its
+ * scratch is the one used), else N2V_ERR_INVALID_ARG.  Returns
  * N2V_ERR_NO_MEM when the call would need more than 512 persistent launches
  * (walk_count / chunk_walkers), otherwise as n2v_walk.  Allocates nothing. */
 int n2v_walk_noalloc(const n2v_graph* g, const int32_t* starts, int64_t n_starts, int32_t r, int32_t l, double p,

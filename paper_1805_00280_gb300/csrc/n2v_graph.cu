@@ -324,6 +324,10 @@ int n2v_graph_load(const int64_t* row_ptr, const int32_t* col, const uint32_t* w
     for (int i = 0; i < 34; ++i) g->info.deg_hist[i] = (int64_t)sc[kScHist + i];
     rc = build_hubs(g, L, s);
   }
+  if (rc == N2V_OK) {
+    g->graph_cache = new_graph_cache();
+    if (!g->graph_cache) rc = N2V_ERR_NO_MEM;
+  }
   if (rc != N2V_OK) {
     free(g);
     return rc;
@@ -342,7 +346,7 @@ int n2v_graph_retune(n2v_graph* g, const n2v_tune* t, void* stream) {
   if (!g || !t || !tune_ok(*t)) return N2V_ERR_INVALID_ARG;
   AuxLayout L = aux_layout(g->n, g->nnz, g->weighted, *t);
   if (L.total > g->aux_bytes) return N2V_ERR_NO_MEM;
-  free_graph_cache(g);
+  clear_graph_cache(g);
   const bool same_hubs = t->hub_count == g->tune.hub_count && t->hub_min_degree == g->tune.hub_min_degree &&
                          t->hub_budget_mb == g->tune.hub_budget_mb;
   g->tune = *t;

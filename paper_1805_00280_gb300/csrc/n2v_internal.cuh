@@ -295,5 +295,7 @@ __device__ __forceinline__ bool approx_decide(int64_t dv, int64_t dt, uint32_t a
 
 // n2v_walk.cu
 LaunchCfg resolve_launch(const n2v_graph* g, int variant);
+void* new_graph_cache();
+void clear_graph_cache(n2v_graph* g);
 void free_graph_cache(n2v_graph* g);
 }  // namespace n2v

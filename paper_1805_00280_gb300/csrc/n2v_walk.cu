@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <new>
 #include <vector>
 
 #include "n2v_step.cuh"
@@ -352,18 +353,28 @@ struct GraphCache {
 
 static bool same_call(const WalkCall& a, const WalkCall& b) { return memcmp(&a, &b, sizeof(WalkCall)) == 0; }
 
-void free_graph_cache(n2v_graph* g) {
+// The cache is created with the handle (n2v_graph_load), so that calls from
+// several threads never race to create it; retuning only empties it.
+void* new_graph_cache() { return new (std::nothrow) GraphCache(); }
+
+void clear_graph_cache(n2v_graph* g) {
   GraphCache* gc = (GraphCache*)g->graph_cache;
   if (!gc) return;
+  std::lock_guard<std::mutex> lock(gc->mu);
   for (auto& e : gc->entries) cudaGraphExecDestroy(e.exec);
-  delete gc;
+  gc->entries.clear();
+}
+
+void free_graph_cache(n2v_graph* g) {
+  clear_graph_cache(g);
+  delete (GraphCache*)g->graph_cache;
   g->graph_cache = nullptr;
 }
 
 static int issue_graph(n2v_graph* g, const WalkCall& c, cudaStream_t s) {
   if (!s) return N2V_ERR_INVALID_ARG;  // the legacy stream cannot be recorded
-  if (!g->graph_cache) g->graph_cache = new GraphCache();
   GraphCache* gc = (GraphCache*)g->graph_cache;
+  if (!gc) return N2V_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lock(gc->mu);
   for (auto& e : gc->entries)
     if (same_call(e.key, c)) return cudaGraphLaunch(e.exec, s) == cudaSuccess ? N2V_OK : N2V_ERR_CUDA;
@@ -597,6 +608,10 @@ extern "C" int n2v_walk_noalloc(const n2v_graph* g, const int32_t* starts, int64
   if (!starts || !walks) return N2V_ERR_INVALID_ARG;
   const int64_t chunks = n_chunks(g, walk_count);
   if (chunks > kNoAllocMaxLaunches) return N2V_ERR_NO_MEM;  // more launch counters than the scratch holds
+  // the scratch used is the current device's: it must be the graph's device
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) return N2V_ERR_CUDA;
+  if (cur != g->device) return N2V_ERR_INVALID_ARG;
   void* scratch = nullptr;
   int rc = noalloc_scratch(&scratch);
   if (rc != N2V_OK) return rc;

@@ -172,6 +172,10 @@ WORKLOADS = {
                         note="weighted R-MAT scale 23, ef 16, w in [1,100], r=4, l=80, p=1, q=0.5"),
     "rmat26": Workload("rmat26", dict(kind="rmat", scale=26, ef=16, seed=1), r=1, l=80, pq=[(2.0, 0.5)],
                        note="R-MAT scale 26, ef 16, r=1, l=80, p=2, q=0.5"),
+    # the scale-26 walk parameters on a graph whose col array (0.5 GB) still exceeds L2: the case
+    # small enough for a full ncu capture of one launch
+    "rmat22": Workload("rmat22", dict(kind="rmat", scale=22, ef=16, seed=1), r=1, l=80, pq=[(2.0, 0.5)],
+                       note="R-MAT scale 22, ef 16, r=1, l=80, p=2, q=0.5"),
     "rmat24serve": Workload("rmat24serve", dict(kind="rmat", scale=24, ef=16, seed=1), r=1, l=80,
                             pq=[], note="serving on R-MAT scale 24, ef 16"),
     # skewed but small enough for a stored transition table (8 sum d^2 = 76 GB)

@@ -63,3 +63,35 @@ def test_noalloc_sub_range_and_rejected_size():
         n2v.n2v_walk_noalloc(graph.handle, starts, g.n, 10, 10, 2.0, 0.5, 9, 0, 40_000, big)
     assert e.value.code == n2v.N2V_ERR_NO_MEM
     graph.close()
+
+
+def test_noalloc_specials_beyond_the_scratch_spill():
+    """On K_800 every step at v from t has 799 special neighbours (t and every other vertex
+    but v).  With 32 shared-memory slots per warp and the spill area the 4 MiB scratch leaves
+    each warp (a few hundred slots at the default grid), the specials of every step overflow
+    both and are enumerated again segment by segment; the rows must still equal n2v_walk's
+    (which keeps them all in its 4096-slot workspace spill) and the oracle's."""
+    import oracle
+
+    k = 800
+    edges = [(i, j) for i in range(k) for j in range(i + 1, k)]
+    g = G.from_edges(k, edges)
+    tune = n2v.default_tune(smem_specials=32, thread_max_deg=0)
+    graph = n2v.Graph.from_csr(g, tune=tune)
+    _, blocks, threads = n2v.n2v_launch_shape(graph.handle)
+    per_warp = ((4 << 20) - 4096) // 4 // (blocks * threads // 32)
+    assert k - 1 > 32 + per_warp, "the clique no longer overflows the scratch spill"
+    starts = torch.arange(k, dtype=torch.int32, device="cuda")
+    r, l, p, q, seed = 8, 12, 0.5, 2.0, 31
+    W = k * r
+    want = n2v.walk(graph, starts, r, l, p, q, seed, "persistent")
+    assert n2v.n2v_stream_status(graph.handle) == n2v.N2V_OK
+    for call in range(2):
+        out = torch.full((W, l), -7, dtype=torch.int32, device="cuda")
+        n2v.n2v_walk_noalloc(graph.handle, starts, k, r, l, p, q, seed, 0, W, out)
+        assert n2v.n2v_stream_status(graph.handle) == n2v.N2V_OK
+        assert torch.equal(out, want), f"call {call}: rows differ from n2v_walk"
+    ids = np.arange(0, W, 7)
+    rows = oracle.walk(g.row_ptr, g.col, None, np.arange(k, dtype=np.int32), l, p, q, seed, ids, threads=8)
+    np.testing.assert_array_equal(want[torch.from_numpy(ids).cuda()].cpu().numpy(), rows)
+    graph.close()
