@@ -425,7 +425,7 @@ def run_ours(args):
     #      evenly over the job
     compare = {}
     ranges = compare_ranges(W, n_start, args, wdef)
-    names = [v for v in args.compare.split(",") if v and v != args.variant and v != "stored"]
+    names = [v for v in args.compare.split(",") if v in ("plain", "binned", "persistent") and v != args.variant]
     if names:
         compare = compare_variants(n2v, graph, starts, n_start, r_total, l, pq, wl.seed, walk_begin, ranges,
                                    [args.variant] + names, outs, ws, stream, dev, world, flush, args.variant)
