@@ -100,7 +100,15 @@ typedef struct n2v_tune {
   int32_t spill_specials;  /* per-warp device-workspace slots for special neighbours that do
                               not fit in shared memory (persistent sampler)                 */
   int32_t stage_buffers;   /* staging windows in flight per warp (2 or 4)                    */
-  int32_t reserved[4];     /* must be zero                                                    */
+  int32_t bitmap_hubs;     /* vertices (largest degree first, whole degree classes, degree >=
+                              hub_min_degree) with a rank bitmap: one bit per vertex of the
+                              graph and a running count per 64 bits (n/4 bytes a hub), so that
+                              "is x in N(h)" and x's index in N(h) take one 16-byte load     */
+  int32_t block_min_deg;   /* 0: warps run their walkers independently.  > 0: the blocks of
+                              the persistent sampler advance 128 walkers together, step by step,
+                              and a step whose longer list has at least this many entries is
+                              taken by the whole block (four warps) instead of one warp      */
+  int32_t reserved[2];     /* must be zero                                                    */
 } n2v_tune;
 
 /* Fill *t with the library defaults. */
@@ -119,13 +127,18 @@ typedef struct n2v_graph_info {
   int64_t hub_slots;      /* total slots of all hub hash sets */
   int64_t deg_hist[34];   /* [0]: degree 0; [i>=1]: degree in [2^(i-1), 2^i) */
   uint32_t w_min, w_max;  /* extreme edge weights (1, 1 when unweighted) */
+  int32_t bitmap_hubs;    /* hubs that received a rank bitmap */
+  int32_t reserved0;
+  int64_t bitmap_min_degree; /* smallest degree among them (0 if none) */
 } n2v_graph_info;
 
 /* Bytes of device memory the caller must provide as `aux` to n2v_graph_load
  * for a graph of this size under tuning `t` (NULL = defaults).  Holds the
  * device status word, degree statistics, the per-edge static weight prefix of
- * weighted graphs (8 bytes per entry) and the hub neighbour-set cache (the
- * GPU counterpart of the FN-Cache neighbour cache, Section 3.4). */
+ * weighted graphs (8 bytes per entry) and the hub neighbour caches (the GPU
+ * counterparts of the FN-Cache neighbour cache, Section 3.4): hashed
+ * neighbour sets (8 bytes per slot) and rank bitmaps (16 bytes per 64
+ * vertices of the graph, per bitmap hub). */
 int n2v_graph_aux_bytes(int64_t n, int64_t nnz, int weighted, const n2v_tune* t, size_t* bytes);
 
 /* Validate a device-resident CSR graph and build its auxiliary structures in
@@ -143,8 +156,9 @@ int n2v_graph_load(const int64_t* row_ptr, const int32_t* col, const uint32_t* w
 int n2v_graph_info_get(const n2v_graph* g, n2v_graph_info* info);
 
 /* Replace the tuning of a loaded graph.  Fields that size `aux` (hub_count,
- * hub_min_degree) must not grow beyond what aux was sized for; the hub cache
- * is rebuilt on `stream`.  Synchronises `stream`. */
+ * hub_budget_mb, bitmap_hubs) must not grow beyond what aux was sized for
+ * (N2V_ERR_NO_MEM); the hub caches are rebuilt on `stream` when a field that
+ * shapes them changed.  Synchronises `stream`. */
 int n2v_graph_retune(n2v_graph* g, const n2v_tune* t, void* stream);
 
 /* Release the handle (and any CUDA graphs recorded on it).  Device buffers
@@ -177,6 +191,32 @@ int n2v_walk_ws_bytes(const n2v_graph* g, int64_t walk_count, int32_t l, int var
 int n2v_walk(const n2v_graph* g, const int32_t* starts, int64_t n_starts, int32_t r, int32_t l, double p,
              double q, uint64_t seed, int64_t walk_begin, int64_t walk_count, int32_t* walks, void* ws,
              size_t ws_bytes, int variant, void* stream);
+
+/* Walks streamed to host memory, for outputs larger than device memory (the
+ * output side of FN-Multi, Section 3.4: walkers run in rounds and each
+ * round's walks are written out before the next).  The walk ids
+ * [walk_begin, walk_begin + walk_count) of the job "r walks from each start"
+ * run in chunks of ring_walks walks, each chunk one n2v_walk call on `stream`
+ * into slot (chunk mod ring_slots) of a device ring; once a chunk is written
+ * its rows are copied to host_walks by one cudaMemcpyAsync on copy_stream,
+ * while the next chunk runs.  A chunk reuses a slot only after that slot's
+ * previous copy finished (events, no host wait).  The rows are those of one
+ * n2v_walk call over the whole range.
+ *   host_walks  host int32 [walk_count][l]; pinned (cudaHostAlloc /
+ *               cudaHostRegister) for the copies to overlap
+ *   dev_ring    device int32 [ring_slots][ring_walks][l], caller-owned
+ *   ring_slots  1 .. 8 (2 lets one chunk compute while the previous copies)
+ *   ws          as for n2v_walk with walk_count = ring_walks
+ *   variant     N2V_PLAIN, N2V_BINNED or N2V_PERSISTENT (no N2V_FLAG_CUDA_GRAPH)
+ *   copy_stream a stream other than `stream` (NULL: the copies go on `stream`
+ *               and do not overlap)
+ * Asynchronous: when `stream` reaches the end of the call's work, every row
+ * is in host_walks (the call makes `stream` wait for the last copies).
+ * Creates and releases a few CUDA events (no device memory). */
+int n2v_walk_stream(const n2v_graph* g, const int32_t* starts, int64_t n_starts, int32_t r, int32_t l, double p,
+                    double q, uint64_t seed, int64_t walk_begin, int64_t walk_count, int32_t* host_walks,
+                    int32_t* dev_ring, int64_t ring_walks, int32_t ring_slots, void* ws, size_t ws_bytes,
+                    int variant, void* stream, void* copy_stream);
 
 /* Allocation-free form of n2v_walk with variant N2V_PERSISTENT, for callers
  * that cannot allocate device memory (code running inside a memory pool or
@@ -239,8 +279,9 @@ int n2v_autotune_ws_bytes(const n2v_graph* g, int64_t sample, int32_t l, size_t*
 
 /* Pick the tuning of the persistent sampler for this graph and job shape:
  * a coordinate descent over stage_window, blocks_per_sm, stream_ratio,
- * thread_max_deg, stage_buffers and (if the graph was loaded with hubs)
- * hub_count, each candidate timed with CUDA events on walks [0, sample) of
+ * thread_max_deg, stage_buffers, smem_specials, block_min_deg and, from none
+ * up to the sizes the graph was loaded with, bitmap_hubs and hub_count,
+ * each candidate timed with CUDA events on walks [0, sample) of
  * the job "one walk from each of starts[0..sample)" (the caller should pass a
  * representative random sample of its start vertices).  A candidate is
  * timed as the faster of two runs (after one untimed run) and replaces the

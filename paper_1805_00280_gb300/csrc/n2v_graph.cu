@@ -41,6 +41,20 @@ AuxLayout aux_layout(int64_t n, int64_t nnz, int weighted, const n2v_tune& t) {
   off += align256(sizeof(int32_t) * (size_t)L.hubs_cap);
   L.hub_slot = off;
   off += align256(sizeof(int2) * (size_t)L.slots_cap);
+  // rank bitmaps: a probe table of at least twice as many slots as hubs, the hub
+  // vertices, and ceil(n/64) 16-byte entries per hub (the data area also holds the
+  // degree counts of the hub selection, 4 (n + 2) bytes, before the bitmaps are built)
+  L.bm_cap = t.bitmap_hubs > 0 ? std::min<int64_t>(t.bitmap_hubs, n) : 0;
+  L.bm_words = (n + 63) / 64;
+  L.bm_bits = 4;
+  while (((int64_t)1 << L.bm_bits) < 2 * L.bm_cap) ++L.bm_bits;
+  L.bm_tab = off;
+  if (L.bm_cap > 0) off += align256(sizeof(int2) * ((size_t)1 << L.bm_bits));
+  L.bm_vtx = off;
+  off += align256(sizeof(int32_t) * (size_t)L.bm_cap);
+  L.bm_data = off;
+  if (L.bm_cap > 0)
+    off += align256(std::max<size_t>(16 * (size_t)L.bm_cap * (size_t)L.bm_words, 4 * ((size_t)n + 2)));
   L.total = off;
   return L;
 }
@@ -155,6 +169,127 @@ __global__ void k_hub_build(const int64_t* __restrict__ rp, const int32_t* __res
   }
 }
 
+// Give every vertex with degree >= dstar a rank bitmap: an index and a slot in
+// the probe table.
+__global__ void k_bm_assign(const int64_t* __restrict__ rp, int64_t n, int64_t dstar, int2* __restrict__ tab,
+                            uint32_t bits, int32_t* __restrict__ bm_vtx, unsigned long long* __restrict__ sc,
+                            int64_t cap) {
+  const uint32_t mask = (1u << bits) - 1u;
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
+    if (rp[u + 1] - rp[u] < dstar) continue;
+    const unsigned long long h = atomicAdd(&sc[kScBmCount], 1ull);
+    if ((int64_t)h >= cap) {
+      atomicOr(&sc[kScBad], 16ull);  // host-side selection guarantees this never happens
+      continue;
+    }
+    bm_vtx[h] = (int32_t)u;
+    uint32_t s = hub_hash((int32_t)u, bits);
+    bool done = false;
+    for (uint32_t probe = 0; probe <= mask && !done; ++probe) {
+      if (atomicCAS(&tab[s].x, -1, (int)u) == -1) {
+        tab[s].y = (int32_t)h;
+        done = true;
+      } else {
+        s = (s + 1u) & mask;
+      }
+    }
+    if (!done) atomicOr(&sc[kScBad], 16ull);
+  }
+}
+
+// One block per bitmap hub: set the bit of every neighbour.
+__global__ void k_bm_fill(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                          const int32_t* __restrict__ bm_vtx, uint4* __restrict__ data, int64_t words) {
+  const int64_t v = bm_vtx[blockIdx.x];
+  uint4* d = data + (int64_t)blockIdx.x * words;
+  for (int64_t j = rp[v] + threadIdx.x; j < rp[v + 1]; j += blockDim.x) {
+    const int32_t x = col[j];
+    atomicOr((unsigned long long*)(d + (x >> 6)), 1ull << (x & 63));
+  }
+}
+
+// One block per bitmap hub: .z of every entry = neighbours in the entries before
+// it (a block-wide exclusive scan of the entries' population counts).
+__global__ void __launch_bounds__(1024) k_bm_rank(uint4* __restrict__ data, int64_t words) {
+  __shared__ uint32_t part[1024];
+  uint4* d = data + (int64_t)blockIdx.x * words;
+  const int64_t per = (words + blockDim.x - 1) / blockDim.x;
+  const int64_t b = threadIdx.x * per, e = min(words, b + per);
+  uint32_t sum = 0;
+  for (int64_t i = b; i < e; ++i) sum += __popc(d[i].x) + __popc(d[i].y);
+  part[threadIdx.x] = sum;
+  __syncthreads();
+  for (int o = 1; o < (int)blockDim.x; o <<= 1) {  // inclusive scan (Hillis-Steele)
+    const uint32_t add = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0u;
+    __syncthreads();
+    part[threadIdx.x] += add;
+    __syncthreads();
+  }
+  uint32_t run = part[threadIdx.x] - sum;
+  for (int64_t i = b; i < e; ++i) {
+    uint4 x = d[i];
+    x.z = run;
+    x.w = 0u;
+    run += __popc(x.x) + __popc(x.y);
+    d[i] = x;
+  }
+}
+
+// Build (or rebuild) the rank bitmaps under g->tune.  Synchronises the stream.
+static int build_bitmaps(n2v_graph* g, const AuxLayout& L, cudaStream_t s) {
+  g->view.bm_data = nullptr;
+  g->view.bm_tab = nullptr;
+  g->view.bm_words = L.bm_words;
+  g->view.bm_bits = L.bm_bits;
+  g->view.bm_min_deg = INT64_MAX;
+  g->info.bitmap_hubs = 0;
+  g->info.bitmap_min_degree = 0;
+  if (L.bm_cap <= 0) return N2V_OK;
+  const int64_t n = g->n;
+  const int64_t maxd = g->info.max_degree;
+  const int64_t dmin = std::max<int64_t>(1, g->tune.hub_min_degree);
+  const int64_t cap = std::min<int64_t>(L.bm_cap, g->tune.bitmap_hubs);
+  if (maxd < dmin || cap <= 0) return N2V_OK;
+  char* aux = (char*)g->aux;
+  uint32_t* count = (uint32_t*)(aux + L.bm_data);  // 4 (maxd + 1) <= 4 (n + 2) bytes
+  const int threads = 256, blocks = g->sms * 8;
+  if (cudaMemsetAsync(count, 0, sizeof(uint32_t) * (size_t)(maxd + 1), s) != cudaSuccess) return N2V_ERR_CUDA;
+  k_degree_counts<<<blocks, threads, 0, s>>>(g->view.rp, n, dmin, count);
+  std::vector<uint32_t> hc((size_t)(maxd + 1 - dmin));
+  if (cudaMemcpyAsync(hc.data(), count + dmin, sizeof(uint32_t) * hc.size(), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return N2V_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return N2V_ERR_CUDA;
+  int64_t hubs = 0, dstar = -1;  // largest degrees first, whole degree classes
+  for (int64_t d = maxd; d >= dmin; --d) {
+    const int64_t c = hc[(size_t)(d - dmin)];
+    if (!c) continue;
+    if (hubs + c > cap) break;
+    hubs += c;
+    dstar = d;
+  }
+  if (dstar < 0 || hubs == 0) return N2V_OK;
+  unsigned long long* sc = g->scratch;
+  cudaError_t e = cudaMemsetAsync(aux + L.bm_tab, 0xff, sizeof(int2) * ((size_t)1 << L.bm_bits), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(aux + L.bm_data, 0, 16 * (size_t)hubs * (size_t)L.bm_words, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(sc + kScBmCount, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return N2V_ERR_CUDA;
+  k_bm_assign<<<blocks, threads, 0, s>>>(g->view.rp, n, dstar, (int2*)(aux + L.bm_tab), L.bm_bits,
+                                         (int32_t*)(aux + L.bm_vtx), sc, hubs);
+  k_bm_fill<<<(unsigned)hubs, 256, 0, s>>>(g->view.rp, g->view.col, (const int32_t*)(aux + L.bm_vtx),
+                                           (uint4*)(aux + L.bm_data), L.bm_words);
+  k_bm_rank<<<(unsigned)hubs, 1024, 0, s>>>((uint4*)(aux + L.bm_data), L.bm_words);
+  unsigned long long bad = 0;
+  if (cudaMemcpyAsync(&bad, sc + kScBad, sizeof(bad), cudaMemcpyDeviceToHost, s) != cudaSuccess) return N2V_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return N2V_ERR_CUDA;
+  if (bad) return N2V_ERR_CUDA;
+  g->view.bm_data = (const uint4*)(aux + L.bm_data);
+  g->view.bm_tab = (const int2*)(aux + L.bm_tab);
+  g->view.bm_min_deg = dstar;
+  g->info.bitmap_hubs = (int32_t)hubs;
+  g->info.bitmap_min_degree = dstar;
+  return N2V_OK;
+}
+
 // Build (or rebuild) the hub cache under g->tune.  Synchronises the stream.
 static int build_hubs(n2v_graph* g, const AuxLayout& L, cudaStream_t s) {
   g->view.hub_of = nullptr;
@@ -164,7 +299,11 @@ static int build_hubs(n2v_graph* g, const AuxLayout& L, cudaStream_t s) {
   g->info.hub_count = 0;
   g->info.hub_min_degree = 0;
   g->info.hub_slots = 0;
-  if (L.hubs_cap <= 0 || L.slots_cap <= 0) return N2V_OK;
+  // the current tuning's caps, inside the layout's (which may be the larger loaded one)
+  const int64_t hubs_cap = std::min<int64_t>(L.hubs_cap, g->tune.hub_count);
+  const int64_t slots_cap =
+      std::min<int64_t>(L.slots_cap, (int64_t)g->tune.hub_budget_mb * (1 << 20) / (int64_t)sizeof(int2));
+  if (hubs_cap <= 0 || slots_cap <= 0) return N2V_OK;
   const int64_t n = g->n;
   const int64_t maxd = g->info.max_degree;
   const int64_t dmin = std::max<int64_t>(1, g->tune.hub_min_degree);
@@ -184,7 +323,7 @@ static int build_hubs(n2v_graph* g, const AuxLayout& L, cudaStream_t s) {
     int64_t c = hc[(size_t)(d - dmin)];
     if (!c) continue;
     int64_t add = c * ((int64_t)1 << table_bits(d));
-    if (hubs + c > L.hubs_cap || slots + add > L.slots_cap) break;
+    if (hubs + c > hubs_cap || slots + add > slots_cap) break;
     hubs += c;
     slots += add;
     dstar = d;
@@ -225,7 +364,8 @@ static bool tune_ok(const n2v_tune& t) {
   if (t.stream_ratio < 0 || t.stream_ratio > 1000000 || t.spill_specials < 0 || t.spill_specials > (1 << 24)) return false;
   if (t.smem_specials % 32) return false;
   if (t.stage_buffers != 2 && t.stage_buffers != 4) return false;
-  for (int i = 0; i < 4; ++i)
+  if (t.bitmap_hubs < 0 || t.bitmap_hubs > 4096 || t.block_min_deg < 0) return false;
+  for (int i = 0; i < 2; ++i)
     if (t.reserved[i]) return false;
   return true;
 }
@@ -286,6 +426,7 @@ int n2v_graph_load(const int64_t* row_ptr, const int32_t* col, const uint32_t* w
   g->aux = aux;
   g->aux_bytes = aux_bytes;
   g->tune = tt;
+  g->tune_loaded = tt;
   char* a = (char*)aux;
   g->status = (uint32_t*)(a + L.status);
   g->scratch = (unsigned long long*)(a + L.scratch);
@@ -323,6 +464,7 @@ int n2v_graph_load(const int64_t* row_ptr, const int32_t* col, const uint32_t* w
     g->info.w_max = weighted && nnz > 0 ? (uint32_t)sc[kScWMax] : 1u;
     for (int i = 0; i < 34; ++i) g->info.deg_hist[i] = (int64_t)sc[kScHist + i];
     rc = build_hubs(g, L, s);
+    if (rc == N2V_OK) rc = build_bitmaps(g, L, s);
   }
   if (rc == N2V_OK) {
     g->graph_cache = new_graph_cache();
@@ -349,8 +491,17 @@ int n2v_graph_retune(n2v_graph* g, const n2v_tune* t, void* stream) {
   clear_graph_cache(g);
   const bool same_hubs = t->hub_count == g->tune.hub_count && t->hub_min_degree == g->tune.hub_min_degree &&
                          t->hub_budget_mb == g->tune.hub_budget_mb;
+  const bool same_bm = t->bitmap_hubs == g->tune.bitmap_hubs && t->hub_min_degree == g->tune.hub_min_degree;
+  // the caches must be built at the layout the graph was loaded with (aux offsets do not move)
+  const AuxLayout L0 = aux_layout(g->n, g->nnz, g->weighted, g->tune_loaded);
+  if (t->hub_count > g->tune_loaded.hub_count || t->hub_budget_mb > g->tune_loaded.hub_budget_mb ||
+      t->bitmap_hubs > g->tune_loaded.bitmap_hubs)
+    return N2V_ERR_NO_MEM;
+  (void)L;
   g->tune = *t;
-  return same_hubs ? N2V_OK : build_hubs(g, L, (cudaStream_t)stream);
+  int rc = same_hubs ? N2V_OK : build_hubs(g, L0, (cudaStream_t)stream);
+  if (rc == N2V_OK && !same_bm) rc = build_bitmaps(g, L0, (cudaStream_t)stream);
+  return rc;
 }
 
 void n2v_graph_free(n2v_graph* g) {

@@ -32,6 +32,14 @@ struct GraphView {
   const int64_t* __restrict__ hub_off;   // [H] first slot of the hub's table
   const uint32_t* __restrict__ hub_bits; // [H] log2 of the table size
   const int2* __restrict__ hub_slot;     // [slots] (neighbour id or -1 if empty, index in the hub's row)
+  // rank bitmaps of the largest hubs (FN-Cache analogue); bm_data null = none.  Entry
+  // bm_data[h * bm_words + (x >> 6)] holds bits 64*(x>>6) .. +63 of N(hub h) as a
+  // 64-bit mask (.x low, .y high) and in .z the number of neighbours below 64*(x>>6).
+  const uint4* __restrict__ bm_data;     // [bitmap hubs][bm_words]
+  const int2* __restrict__ bm_tab;       // [2^bm_bits] (hub vertex or -1, bitmap index)
+  int64_t bm_words;                      // ceil(n / 64)
+  int64_t bm_min_deg;                    // smallest degree of a bitmap hub
+  uint32_t bm_bits;
 };
 
 // One walk job slice, as every sampler sees it.
@@ -66,6 +74,7 @@ struct LaunchCfg {
   int spill_specials;  // per warp, in the device workspace (persistent sampler only)
   int stage_buffers;   // staging windows per warp (2 or 4)
   int minb;            // persistent kernel instance: resident 128-thread blocks per SM it is compiled for
+  int block_min_deg;   // persistent sampler: 0 = warps independent; > 0 = block batches with a block tier
 };
 
 // Shared memory of one warp: four mbarrier slots (32 bytes), the specials
@@ -218,6 +227,7 @@ struct n2v_graph {
   uint32_t* status;        // device status word
   unsigned long long* scratch;  // device scratch words inside aux
   n2v_tune tune;
+  n2v_tune tune_loaded;    // the tuning aux was laid out for (n2v_graph_load)
   n2v_graph_info info;
   int device;
   int sms;
@@ -248,10 +258,34 @@ __device__ __forceinline__ int32_t hub_find(const GraphView& g, int32_t h, int32
   return -1;
 }
 
+// Bitmap index of hub vertex v, or -1 (open addressing, table at most half full).
+__device__ __forceinline__ int32_t bm_find(const GraphView& g, int32_t v) {
+  const uint32_t mask = (1u << g.bm_bits) - 1u;
+  uint32_t s = hub_hash(v, g.bm_bits);
+  for (uint32_t probe = 0; probe <= mask; ++probe) {
+    const int2 e = __ldg(g.bm_tab + s);
+    if (e.x == v) return e.y;
+    if (e.x < 0) return -1;
+    s = (s + 1u) & mask;
+  }
+  return -1;
+}
+
+// Index of x inside the CSR row of bitmap hub h, or -1 when x is not a
+// neighbour: one 16-byte load, a bit test and a population count.
+__device__ __forceinline__ int32_t bm_pos(const GraphView& g, int32_t h, int32_t x) {
+  const uint4 e = __ldg(g.bm_data + (int64_t)h * g.bm_words + (x >> 6));
+  const uint64_t bits = ((uint64_t)e.y << 32) | (uint64_t)e.x;
+  const int b = x & 63;
+  if (!((bits >> b) & 1ull)) return -1;
+  return (int32_t)e.z + __popcll(bits & ((1ull << b) - 1ull));
+}
+
 // Layout of the caller's auxiliary buffer (byte offsets, 256-aligned).
 struct AuxLayout {
-  size_t status, scratch, wpre, hub_of, hub_off, hub_bits, hub_vtx, hub_slot, total;
-  int64_t hubs_cap, slots_cap;
+  size_t status, scratch, wpre, hub_of, hub_off, hub_bits, hub_vtx, hub_slot, bm_tab, bm_vtx, bm_data, total;
+  int64_t hubs_cap, slots_cap, bm_cap, bm_words;
+  uint32_t bm_bits;
 };
 AuxLayout aux_layout(int64_t n, int64_t nnz, int weighted, const n2v_tune& t);
 
@@ -266,6 +300,7 @@ enum : int {
   kScWMin = 42,
   kScWMax = 43,
   kScSumDeg2 = 44,  // sum over edges of deg(target): entries of a stored transition table
+  kScBmCount = 45,  // bitmap hubs assigned
   kScWords = 64
 };
 

@@ -131,6 +131,9 @@ struct StepCtx {
   int ins;         // index of t inside S = N(t) + {t}
   bool has_self;   // t already in N(t) (self-loop at t)
   int slen;        // |S|
+  // the candidates a generator walks, [cb, ce) of the shorter list (ce < 0: to its end),
+  // and the part [lb, le) of the longer list a staging generator streams (le < 0: to its end)
+  int cb, ce, lb, le;
 };
 
 // i-th element of S = N(t) + {t} (sorted, no duplicate)
@@ -279,9 +282,41 @@ __device__ __forceinline__ void sink_emit(SpecialSink& k, WarpSmem& sm, const Gr
 // Enumerate the specials of the step in increasing position into `k`.
 // mode 0: probe over N(v) (membership in N(t)); 1: probe over S (position in
 // N(v)); 2: stage N(v), candidates S; 3: stage N(t), candidates N(v).
-__device__ __forceinline__ void gen_specials(StepCtx& c, int mode, int32_t hub, WarpSmem& sm, SpecialSink& k,
-                                             uint32_t a_p, uint32_t a_q, int lane) {
+// hub >= 0: the longer list is that hub's hashed set; bm >= 0: it has a rank
+// bitmap (the probe modes only).
+__device__ __forceinline__ void gen_specials(StepCtx& c, int mode, int32_t hub, int32_t bm, WarpSmem& sm,
+                                             SpecialSink& k, uint32_t a_p, uint32_t a_q, int lane) {
   const GraphView& g = *c.g;
+  if (mode == 0 && bm >= 0) {
+    // N(t) is a bitmap hub: two independent one-load membership tests per lane and chunk
+    const int ce = c.ce < 0 ? c.dv : c.ce;
+    for (int c0 = c.cb; c0 < ce; c0 += 64) {
+      const int i0 = c0 + lane, i1 = c0 + 32 + lane;
+      const int32_t x0 = i0 < ce ? __ldg(c.nv + i0) : 0;
+      const int32_t x1 = i1 < ce ? __ldg(c.nv + i1) : 0;
+      const bool in0 = i0 < ce && bm_pos(g, bm, x0) >= 0;
+      const bool in1 = i1 < ce && bm_pos(g, bm, x1) >= 0;
+      const bool sp0 = i0 < ce && (x0 == c.t32 || in0);
+      const bool sp1 = i1 < ce && (x1 == c.t32 || in1);
+      sink_emit(k, sm, g, c.bv, sp0 ? i0 : -1, sp0 ? (x0 == c.t32 ? 2u : 1u) : 0u, a_p, a_q, lane);
+      if (c0 + 32 < ce) sink_emit(k, sm, g, c.bv, sp1 ? i1 : -1, sp1 ? (x1 == c.t32 ? 2u : 1u) : 0u, a_p, a_q, lane);
+    }
+    return;
+  }
+  if (mode == 1 && bm >= 0) {
+    // N(v) is a bitmap hub: each element of S = N(t) + {t} finds its index in N(v) by one load
+    const int ce = c.ce < 0 ? c.slen : c.ce;
+    for (int c0 = c.cb; c0 < ce; c0 += 64) {
+      const int i0 = c0 + lane, i1 = c0 + 32 + lane;
+      const int32_t y0 = i0 < ce ? s_at(c, i0) : 0;
+      const int32_t y1 = i1 < ce ? s_at(c, i1) : 0;
+      const int32_t p0 = i0 < ce ? bm_pos(g, bm, y0) : -1;
+      const int32_t p1 = i1 < ce ? bm_pos(g, bm, y1) : -1;
+      sink_emit(k, sm, g, c.bv, p0, p0 >= 0 ? (y0 == c.t32 ? 2u : 1u) : 0u, a_p, a_q, lane);
+      if (c0 + 32 < ce) sink_emit(k, sm, g, c.bv, p1, p1 >= 0 ? (y1 == c.t32 ? 2u : 1u) : 0u, a_p, a_q, lane);
+    }
+    return;
+  }
   if (mode == 0) {
     // two candidates per lane and chunk: two independent searches in flight
     auto member = [&](int32_t x) -> bool {
@@ -290,10 +325,11 @@ __device__ __forceinline__ void gen_specials(StepCtx& c, int mode, int32_t hub, 
       const int p = lower_bound32(c.nt, c.dt, x);
       return p < c.dt && __ldg(c.nt + p) == x;
     };
-    for (int c0 = 0; c0 < c.dv; c0 += 64) {
+    const int ce = c.ce < 0 ? c.dv : c.ce;
+    for (int c0 = c.cb; c0 < ce; c0 += 64) {
       const int i0 = c0 + lane, i1 = c0 + 32 + lane;
-      const int32_t x0 = i0 < c.dv ? __ldg(c.nv + i0) : -1;
-      const int32_t x1 = i1 < c.dv ? __ldg(c.nv + i1) : -1;
+      const int32_t x0 = i0 < ce ? __ldg(c.nv + i0) : -1;
+      const int32_t x1 = i1 < ce ? __ldg(c.nv + i1) : -1;
       bool sp0 = false, sp1 = false;
       if (hub < 0) {
         // interleaved lower bounds over N(t)
@@ -311,23 +347,24 @@ __device__ __forceinline__ void gen_specials(StepCtx& c, int mode, int32_t hub, 
             n1 = a1 ? n1 - h1 - 1 : h1;
           }
         }
-        sp0 = i0 < c.dv && (x0 == c.t32 || (lo0 < c.dt && __ldg(c.nt + lo0) == x0));
-        sp1 = i1 < c.dv && (x1 == c.t32 || (lo1 < c.dt && __ldg(c.nt + lo1) == x1));
+        sp0 = i0 < ce && (x0 == c.t32 || (lo0 < c.dt && __ldg(c.nt + lo0) == x0));
+        sp1 = i1 < ce && (x1 == c.t32 || (lo1 < c.dt && __ldg(c.nt + lo1) == x1));
       } else {
-        sp0 = i0 < c.dv && member(x0);
-        sp1 = i1 < c.dv && member(x1);
+        sp0 = i0 < ce && member(x0);
+        sp1 = i1 < ce && member(x1);
       }
       sink_emit(k, sm, g, c.bv, sp0 ? i0 : -1, sp0 ? (x0 == c.t32 ? 2u : 1u) : 0u, a_p, a_q, lane);
-      if (c0 + 32 < c.dv) sink_emit(k, sm, g, c.bv, sp1 ? i1 : -1, sp1 ? (x1 == c.t32 ? 2u : 1u) : 0u, a_p, a_q, lane);
+      if (c0 + 32 < ce) sink_emit(k, sm, g, c.bv, sp1 ? i1 : -1, sp1 ? (x1 == c.t32 ? 2u : 1u) : 0u, a_p, a_q, lane);
     }
     return;
   }
   if (mode == 1) {
-    for (int c0 = 0; c0 < c.slen; c0 += 32) {
+    const int ce = c.ce < 0 ? c.slen : c.ce;
+    for (int c0 = c.cb; c0 < ce; c0 += 32) {
       const int i = c0 + lane;
       int32_t pos = -1;
       uint32_t cls = 0;
-      if (i < c.slen) {
+      if (i < ce) {
         const int32_t y = s_at(c, i);
         int p;
         if (hub >= 0) {
@@ -348,8 +385,8 @@ __device__ __forceinline__ void gen_specials(StepCtx& c, int mode, int32_t hub, 
   // stage: the longer list flows through the two windows; the candidates of
   // each chunk are searched in the resident window
   const bool stage_v = mode == 2;
-  const int32_t* L = stage_v ? c.nv : c.nt;
-  const int llen = stage_v ? c.dv : c.dt;
+  const int32_t* L = (stage_v ? c.nv : c.nt) + c.lb;
+  const int llen = (c.le < 0 ? (stage_v ? c.dv : c.dt) : c.le) - c.lb;  // > 0 (the callers ensure it)
   const int W = sm.wlen;
   const int nwin = (llen + W - 1) / W;
   const int ahead = min(sm.nbuf, nwin);
@@ -359,7 +396,7 @@ __device__ __forceinline__ void gen_specials(StepCtx& c, int mode, int32_t hub, 
     c.has_self = c.ins < c.dt && __ldg(c.nt + c.ins) == c.t32;
     c.slen = c.dt + (c.has_self ? 0 : 1);
   }
-  const int nkeys = stage_v ? c.slen : c.dv;
+  const int nkeys = c.ce < 0 ? (stage_v ? c.slen : c.dv) : c.ce;  // keys [c.cb, nkeys)
   int wi = 0;
   // two keys per lane and chunk (keys kc + lane and kc + 32 + lane): two
   // independent search chains in flight per lane
@@ -391,11 +428,11 @@ __device__ __forceinline__ void gen_specials(StepCtx& c, int mode, int32_t hub, 
     wlast_inf = wj == nwin - 1;
     wlast = lds32(wbase + 4u * (uint32_t)(wcnt - 1));
   };
-  int32_t next0 = key_at(lane), next1 = key_at(32 + lane);
-  int32_t after0 = key_at(64 + lane), after1 = key_at(96 + lane);
+  int32_t next0 = key_at(c.cb + lane), next1 = key_at(c.cb + 32 + lane);
+  int32_t after0 = key_at(c.cb + 64 + lane), after1 = key_at(c.cb + 96 + lane);
   land(0);
   set_window(0);
-  for (int kc = 0; kc < nkeys; kc += 64) {
+  for (int kc = c.cb; kc < nkeys; kc += 64) {
     const int i0 = kc + lane, i1 = kc + 32 + lane;
     const int32_t key0 = next0, key1 = next1;
     next0 = after0;
@@ -416,8 +453,8 @@ __device__ __forceinline__ void gen_specials(StepCtx& c, int mode, int32_t hub, 
         window_rank2_any(wdepth, wbase, key0, key1, lo0, lo1);
         if (lo0 < wcnt && lds32(wbase + 4u * lo0) < key0) ++lo0;
         if (lo1 < wcnt && lds32(wbase + 4u * lo1) < key1) ++lo1;
-        if (go0 && lo0 < wcnt && lds32(wbase + 4u * lo0) == key0) at0 = wi * W + lo0;
-        if (go1 && lo1 < wcnt && lds32(wbase + 4u * lo1) == key1) at1 = wi * W + lo1;
+        if (go0 && lo0 < wcnt && lds32(wbase + 4u * lo0) == key0) at0 = c.lb + wi * W + lo0;
+        if (go1 && lo1 < wcnt && lds32(wbase + 4u * lo1) == key1) at1 = c.lb + wi * W + lo1;
         pend0 = pend0 && !go0;
         pend1 = pend1 && !go1;
       }
@@ -456,50 +493,44 @@ __device__ __forceinline__ void gen_specials(StepCtx& c, int mode, int32_t hub, 
   for (int q = wi + 1; q < nwin && q <= wi + sm.nbuf - 1; ++q) stage_wait(sm, q & (sm.nbuf - 1));
 }
 
-// bv, ev: row bounds of v; bt, et: row bounds of t (k >= 1)
-__device__ __forceinline__ int32_t warp_step(const GraphView& g, int64_t t, int64_t v, int64_t bv, int64_t ev,
-                                             int64_t bt, int64_t et, int k, uint64_t u, uint32_t a_p, uint32_t a_q,
-                                             WarpSmem& sm, int stream_ratio, int lane) {
-  const int64_t dv = ev - bv;
-  if (dv == 0) return -1;
-  const int32_t* __restrict__ nv = g.col + bv;
-  if (k == 0) {
-    if (!g.w) return __ldg(nv + (int64_t)scale_draw(u, (uint64_t)dv));
-    const uint64_t T0 = __ldg(g.wpre + ev - 1);
-    if (T0 == 0) return -1;
-    return __ldg(nv + warp_first_above_u64(g.wpre + bv, 0, dv - 1, scale_draw(u, T0), lane));
-  }
-  StepCtx c;
-  c.g = &g;
-  c.bv = bv;
-  c.dv = (int)dv;
-  c.dt = (int)(et - bt);
-  c.nv = nv;
-  c.nt = g.col + bt;
-  c.t32 = (int32_t)t;
-  c.ins = -1;          // t's slot in S: found only by the modes that walk S
-  c.has_self = false;
-  c.slen = c.dt + 1;   // |S| unless t has a self-loop; fixed where S is walked
-  const uint64_t Wv = g.w ? __ldg(g.wpre + ev - 1) : (uint64_t)dv;
+// How a step enumerates its specials (the generator modes of gen_specials) and
+// which hub structure, if any, serves its longer list.
+struct StepPlan {
+  int mode;
+  int32_t hub, bm;
+};
 
+// Identical in every lane (and in every warp of a block that shares the step).
+__device__ __forceinline__ StepPlan plan_step(StepCtx& c, const GraphView& g, int64_t t, int64_t v,
+                                              const WarpSmem& sm, int stream_ratio) {
   const bool v_short = c.dv <= c.slen;
   const int shorter = v_short ? c.dv : c.slen;
   const int longer = v_short ? c.dt : c.dv;  // the list that would be staged
   const int64_t probe_cost = 32ll * ((shorter + 31) / 32) * (ceil_log2(longer + 1) + 1);
-  int mode;
-  int32_t hub = -1;
-  if (sm.wlen > 0 && longer > 64 && longer * 10 <= (int64_t)stream_ratio * probe_cost) {
-    mode = v_short ? 3 : 2;
+  StepPlan pl;
+  pl.hub = -1;
+  pl.bm = -1;
+  // a longer list with a rank bitmap is always probed: one independent load per candidate
+  if (g.bm_data && longer >= g.bm_min_deg) pl.bm = bm_find(g, (int32_t)(v_short ? t : v));
+  if (pl.bm >= 0) {
+    pl.mode = v_short ? 0 : 1;
+  } else if (sm.wlen > 0 && longer > 64 && longer * 10 <= (int64_t)stream_ratio * probe_cost) {
+    pl.mode = v_short ? 3 : 2;
   } else {
-    mode = v_short ? 0 : 1;
-    if (g.hub_of) hub = __ldg(g.hub_of + (v_short ? t : v));
+    pl.mode = v_short ? 0 : 1;
+    if (g.hub_of) pl.hub = __ldg(g.hub_of + (v_short ? t : v));
   }
-  if (mode == 1) {  // walks S = N(t) + {t} in order (mode 2 finds t's slot while its copies fly)
-    c.ins = lower_bound32(c.nt, c.dt, c.t32);
-    c.has_self = c.ins < c.dt && __ldg(c.nt + c.ins) == c.t32;
-    c.slen = c.dt + (c.has_self ? 0 : 1);
-  }
+  return pl;
+}
 
+// t's slot in S = N(t) + {t} (the modes that walk S need it).
+__device__ __forceinline__ void find_t_slot(StepCtx& c) {
+  c.ins = lower_bound32(c.nt, c.dt, c.t32);
+  c.has_self = c.ins < c.dt && __ldg(c.nt + c.ins) == c.t32;
+  c.slen = c.dt + (c.has_self ? 0 : 1);
+}
+
+__device__ __forceinline__ SpecialSink new_sink(const WarpSmem& sm) {
   SpecialSink sk;
   sk.cnt = 0;
   sk.ord_t = -1;
@@ -507,25 +538,43 @@ __device__ __forceinline__ int32_t warp_step(const GraphView& g, int64_t t, int6
   sk.skip = 0;
   sk.cap = sm.cap;  // positions are packed in 30 bits: degrees < 2^30 (checked at load)
   sk.keep = sk.cap + sm.spill_cap;
+  return sk;
+}
 
-  uint64_t r = 0, D = 0;
-  int prev = -1, chosen = -1;
+// Sum of (alpha - a_q) * w over the specials the sink saw (whole warp).
+__device__ __forceinline__ uint64_t sink_correction(const GraphView& g, const SpecialSink& sk, uint32_t a_p,
+                                                    uint32_t a_q) {
+  if (g.w) return warp_sum_u64(sk.dpart);
+  const uint64_t d1 = (uint64_t)kAlphaOne - (uint64_t)a_q, d2 = (uint64_t)a_p - (uint64_t)a_q;
+  return (uint64_t)(sk.cnt - (sk.ord_t >= 0 ? 1 : 0)) * d1 + (sk.ord_t >= 0 ? d2 : 0ull);
+}
+
+// Static prefix W_j = sum of w over N(v) up to position j (W_{-1} = 0).
+__device__ __forceinline__ uint64_t static_prefix(const GraphView& g, int64_t bv, int j) {
+  return j < 0 ? 0ull : (g.w ? __ldg(g.wpre + bv + j) : (uint64_t)(j + 1));
+}
+
+// The chosen position, given that it lies in the position range (prev0, hi]
+// of N(v), that C_j = a_q W_j + D_j with D = D0 just before the range, and
+// that `sk` holds the first enumeration of the range's specials (those with
+// ordinals [0, keep) kept).  Pass 2 walks the kept specials in position order;
+// if the answer lies beyond them, the range is enumerated again keeping the
+// next segment, and the walk continues from where it stopped.
+__device__ __forceinline__ int select_range(StepCtx& c, const StepPlan& pl, WarpSmem& sm, SpecialSink& sk,
+                                            uint64_t r, uint64_t D0, int prev0, int hi_pos, uint32_t a_p,
+                                            uint32_t a_q, int lane) {
+  const GraphView& g = *c.g;
+  const int64_t bv = c.bv;
+  uint64_t D = D0;
+  int prev = prev0, chosen = -1;
   bool found = false;
   const uint64_t d1 = (uint64_t)kAlphaOne - (uint64_t)a_q, d2 = (uint64_t)a_p - (uint64_t)a_q;
-  // Pass 1 enumerates every special (and sums the corrections into T); pass 2
-  // walks the kept specials in position order.  If the answer lies beyond
-  // the kept ones, the specials are enumerated again, keeping the next
-  // segment, and the walk continues from where it stopped.
   for (int seg = 0;; seg += sk.keep) {
-    sk.cnt = 0;
-    sk.skip = seg;
-    gen_specials(c, mode, hub, sm, sk, a_p, a_q, lane);
-    if (seg == 0) {
-      const uint64_t corr = g.w ? warp_sum_u64(sk.dpart)
-                                : (uint64_t)(sk.cnt - (sk.ord_t >= 0 ? 1 : 0)) * d1 + (sk.ord_t >= 0 ? d2 : 0ull);
-      const uint64_t T = (uint64_t)a_q * Wv + corr;
-      if (T == 0) return -1;
-      r = scale_draw(u, T);
+    if (seg > 0) {
+      sk.cnt = 0;
+      sk.ord_t = -1;
+      sk.skip = seg;
+      gen_specials(c, pl.mode, pl.hub, pl.bm, sm, sk, a_p, a_q, lane);
     }
     __syncwarp();
     __threadfence_block();  // spilled specials are read back by other lanes
@@ -536,7 +585,7 @@ __device__ __forceinline__ int32_t warp_step(const GraphView& g, int64_t t, int6
       // C > r is found by a 32-way search over the ordinals.
       auto spec_at = [&](int m) -> int { return (int)((m < sk.cap ? sm.spec[m] : sm.spill[m - sk.cap]) & 0x3fffffffu); };
       auto Dm = [&](int m) -> uint64_t {
-        return m < 0 ? 0ull : (uint64_t)(m + 1) * d1 + ((sk.ord_t >= 0 && m >= sk.ord_t) ? d2 - d1 : 0ull);
+        return m < 0 ? D0 : D0 + (uint64_t)(m + 1) * d1 + ((sk.ord_t >= 0 && m >= sk.ord_t) ? d2 - d1 : 0ull);
       };
       int lo = 0, hi = sk.cnt;  // first m in [lo, hi) with C(pos_m) > r, hi if none
       while (hi - lo > 0) {
@@ -559,7 +608,7 @@ __device__ __forceinline__ int32_t warp_step(const GraphView& g, int64_t t, int6
       }
       if (hi < sk.cnt) {
         const int fpos = spec_at(hi);
-        prev = hi > 0 ? spec_at(hi - 1) : -1;
+        prev = hi > 0 ? spec_at(hi - 1) : prev0;
         D = Dm(hi - 1);
         if ((uint64_t)a_q * (uint64_t)fpos + D > r) {
           chosen = fpos - 1;  // in the gap (prev, fpos - 1]
@@ -568,7 +617,7 @@ __device__ __forceinline__ int32_t warp_step(const GraphView& g, int64_t t, int6
           found = true;
         }
       } else {
-        prev = sk.cnt > 0 ? spec_at(sk.cnt - 1) : -1;
+        prev = sk.cnt > 0 ? spec_at(sk.cnt - 1) : prev0;
         D = Dm(sk.cnt - 1);
       }
       break;
@@ -586,7 +635,7 @@ __device__ __forceinline__ int32_t warp_step(const GraphView& g, int64_t t, int6
       const uint64_t dl = special_delta(g, bv, pos, cls, a_p, a_q);
       const uint64_t incl = warp_incl_scan_u64(dl, lane) + D;
       const uint64_t excl = incl - dl;
-      const uint64_t Wp = pos < 0 ? 0ull : (g.w ? __ldg(g.wpre + bv + pos) : (uint64_t)(pos + 1));
+      const uint64_t Wp = pos < 0 ? 0ull : static_prefix(g, bv, pos);
       const bool hit = cls != 0u && ((uint64_t)a_q * Wp + incl > r);
       const unsigned hm = __ballot_sync(kFull, hit);
       const unsigned smask = __ballot_sync(kFull, cls != 0u);
@@ -597,7 +646,7 @@ __device__ __forceinline__ int32_t warp_step(const GraphView& g, int64_t t, int6
         const unsigned below = smask & ((1u << f) - 1u);
         const int pp = __shfl_sync(kFull, pos, below ? 31 - __clz(below) : 0);
         const int gap_lo = below ? pp : prev;
-        const uint64_t Wb = fpos - 1 < 0 ? 0ull : (g.w ? __ldg(g.wpre + bv + fpos - 1) : (uint64_t)fpos);
+        const uint64_t Wb = static_prefix(g, bv, fpos - 1);
         if ((uint64_t)a_q * Wb + fexcl > r) {
           prev = gap_lo;
           D = fexcl;
@@ -617,7 +666,7 @@ __device__ __forceinline__ int32_t warp_step(const GraphView& g, int64_t t, int6
   }
   if (!found) {
     // first j in (prev, hi] with a_q * W_j + D > r
-    const int hi = chosen >= 0 ? chosen : c.dv - 1;
+    const int hi = chosen >= 0 ? chosen : hi_pos;
     const uint64_t m = (r - D) / (uint64_t)a_q;
     if (!g.w) {
       chosen = m > (uint64_t)hi ? hi : (int)m;
@@ -626,8 +675,138 @@ __device__ __forceinline__ int32_t warp_step(const GraphView& g, int64_t t, int6
       chosen = (int)warp_first_above_u64(g.wpre + bv, prev + 1, hi, m, lane);
     }
   }
+  return chosen;
+}
+
+__device__ __forceinline__ StepCtx step_ctx(const GraphView& g, int64_t t, int64_t bv, int64_t ev, int64_t bt,
+                                            int64_t et) {
+  StepCtx c;
+  c.g = &g;
+  c.bv = bv;
+  c.dv = (int)(ev - bv);
+  c.dt = (int)(et - bt);
+  c.nv = g.col + bv;
+  c.nt = g.col + bt;
+  c.t32 = (int32_t)t;
+  c.ins = -1;          // t's slot in S: found only by the modes that walk S
+  c.has_self = false;
+  c.slen = c.dt + 1;   // |S| unless t has a self-loop; fixed where S is walked
+  c.cb = 0;
+  c.ce = -1;
+  c.lb = 0;
+  c.le = -1;
+  return c;
+}
+
+// bv, ev: row bounds of v; bt, et: row bounds of t (k >= 1)
+__device__ __forceinline__ int32_t warp_step(const GraphView& g, int64_t t, int64_t v, int64_t bv, int64_t ev,
+                                             int64_t bt, int64_t et, int k, uint64_t u, uint32_t a_p, uint32_t a_q,
+                                             WarpSmem& sm, int stream_ratio, int lane) {
+  const int64_t dv = ev - bv;
+  if (dv == 0) return -1;
+  const int32_t* __restrict__ nv = g.col + bv;
+  if (k == 0) {
+    if (!g.w) return __ldg(nv + (int64_t)scale_draw(u, (uint64_t)dv));
+    const uint64_t T0 = __ldg(g.wpre + ev - 1);
+    if (T0 == 0) return -1;
+    return __ldg(nv + warp_first_above_u64(g.wpre + bv, 0, dv - 1, scale_draw(u, T0), lane));
+  }
+  StepCtx c = step_ctx(g, t, bv, ev, bt, et);
+  const StepPlan pl = plan_step(c, g, t, v, sm, stream_ratio);
+  if (pl.mode == 1) find_t_slot(c);  // walks S in order (mode 2 finds t's slot while its copies fly)
+  // pass 1: every special (their corrections give T), the first `keep` of them kept
+  SpecialSink sk = new_sink(sm);
+  gen_specials(c, pl.mode, pl.hub, pl.bm, sm, sk, a_p, a_q, lane);
+  const uint64_t Wv = static_prefix(g, bv, c.dv - 1);
+  const uint64_t T = (uint64_t)a_q * Wv + sink_correction(g, sk, a_p, a_q);
+  if (T == 0) return -1;
+  const int chosen = select_range(c, pl, sm, sk, scale_draw(u, T), 0ull, -1, c.dv - 1, a_p, a_q, lane);
   __syncwarp();
   return __ldg(nv + chosen);
+}
+
+// ---------------------------------------------------------------------------
+// Whole block (four warps), one step.  Every thread of the block must call it
+// with the same arguments; it synchronises the block twice.
+//
+// The candidates of the step (the shorter list, as in warp_step) are split
+// into four contiguous quarters, one per warp.  Because both lists are sorted,
+// the specials warp w finds all lie in a position range [P_w, P_{w+1}) of
+// N(v), and the four ranges tile N(v) in order.  Each warp enumerates its
+// quarter into its own shared-memory specials (staging only the part of the
+// longer list its quarter can meet); a block-wide exclusive scan of the four
+// corrections gives T and, per range, D just before it.  The range whose end
+// value C exceeds r = floor(u T / 2^64) while the value before it does not
+// holds the answer, and its warp finishes the step as warp_step does.
+struct BlockScratch {
+  uint64_t corr[4];
+  int32_t pos[4];   // P_w
+  int32_t result;
+};
+
+__device__ __forceinline__ int32_t block_step(const GraphView& g, int64_t t, int64_t v, int k, uint64_t u,
+                                              uint32_t a_p, uint32_t a_q, WarpSmem& sm, BlockScratch* bs, int wib,
+                                              int stream_ratio, int lane) {
+  const int64_t bv = g.rp[v], ev = g.rp[v + 1];
+  const int64_t dv = ev - bv;
+  if (dv == 0) return -1;
+  if (k == 0) return warp_step(g, t, v, bv, ev, 0, 0, 0, u, a_p, a_q, sm, stream_ratio, lane);
+  const int64_t bt = g.rp[t], et = g.rp[t + 1];
+  StepCtx c = step_ctx(g, t, bv, ev, bt, et);
+  StepPlan pl = plan_step(c, g, t, v, sm, stream_ratio);
+  const bool cand_v = pl.mode == 0 || pl.mode == 3;  // candidates: N(v) (positions) or S
+  if (!cand_v) find_t_slot(c);
+  const int nc = cand_v ? c.dv : c.slen;
+  const int per = (((nc + 3) >> 2) + 63) & ~63;  // whole 64-candidate chunks per warp
+  const int cb = min(nc, wib * per), ce = min(nc, cb + per);
+  // P(i): the first position of N(v) a candidate >= the i-th can meet
+  auto pos_of = [&](int i) -> int {
+    if (i == 0) return 0;
+    if (i >= nc) return c.dv;
+    return cand_v ? i : lower_bound32(c.nv, c.dv, s_at(c, i));
+  };
+  const int P_lo = pos_of(cb), P_hi = pos_of(ce);
+  c.cb = cb;
+  c.ce = ce;
+  if (pl.mode == 2) {  // stage N(v): only the positions this quarter can reach
+    c.lb = P_lo;
+    c.le = P_hi;
+  } else if (pl.mode == 3) {  // stage N(t): only the elements this quarter's keys can equal
+    c.lb = cb >= nc ? c.dt : (cb == 0 ? 0 : lower_bound32(c.nt, c.dt, __ldg(c.nv + cb)));
+    c.le = ce >= nc ? c.dt : lower_bound32(c.nt, c.dt, __ldg(c.nv + ce));
+  }
+  if ((pl.mode == 2 || pl.mode == 3) && c.le <= c.lb) {
+    pl.mode = pl.mode == 2 ? 1 : 0;  // nothing to stream: probe the whole longer list, same candidates
+    c.lb = 0;
+    c.le = -1;
+  }
+  SpecialSink sk = new_sink(sm);
+  if (cb < ce) gen_specials(c, pl.mode, pl.hub, pl.bm, sm, sk, a_p, a_q, lane);
+  const uint64_t corr = sink_correction(g, sk, a_p, a_q);
+  if (lane == 0) {
+    bs->corr[wib] = corr;
+    bs->pos[wib] = P_lo;
+  }
+  __syncthreads();
+  uint64_t T = (uint64_t)a_q * static_prefix(g, bv, c.dv - 1), Dw = 0;
+  for (int w = 0; w < 4; ++w) {
+    const uint64_t cw = bs->corr[w];
+    T += cw;
+    if (w < wib) Dw += cw;
+  }
+  int32_t res = -1;
+  if (T != 0) {
+    const uint64_t r = scale_draw(u, T);
+    const uint64_t C_before = (uint64_t)a_q * static_prefix(g, bv, P_lo - 1) + Dw;
+    const uint64_t C_end = (uint64_t)a_q * static_prefix(g, bv, P_hi - 1) + Dw + corr;
+    if (P_lo < P_hi && C_before <= r && r < C_end) {
+      const int j = select_range(c, pl, sm, sk, r, Dw, P_lo - 1, P_hi - 1, a_p, a_q, lane);
+      if (lane == 0) bs->result = __ldg(c.nv + j);
+    }
+  }
+  __syncthreads();
+  if (T != 0) res = bs->result;
+  return res;
 }
 
 // ---------------------------------------------------------------------------
@@ -657,6 +836,56 @@ __device__ __forceinline__ int32_t static_step(const GraphView& g, int64_t bv, i
 __device__ __forceinline__ bool approx_here(const WalkJob& J, int k, int64_t dv, int64_t dt) {
   return J.approx && k > 0 && dv >= J.approx_popular && dt < J.approx_popular &&
          approx_decide(dv, dt, J.a_p, J.a_q, J.w_min, J.w_max, J.approx_eps);
+}
+
+// ---------------------------------------------------------------------------
+// Output of one walker's row: the vertices of steps 4m .. 4m+3 are kept in
+// registers and written by one 16-byte store where the row is 16-byte aligned
+// (one sector touched per four steps instead of one per step), else one by one.
+struct RowOut {
+  int32_t* row;
+  int32_t o0, o1, o2;
+  bool vec;
+};
+
+__device__ __forceinline__ RowOut row_out(int32_t* row) {
+  RowOut b;
+  b.row = row;
+  b.o0 = b.o1 = b.o2 = -1;
+  b.vec = ((uintptr_t)row & 15) == 0;
+  return b;
+}
+
+// Record step k's vertex y (k is the same in every lane of the warp).
+__device__ __forceinline__ void row_put(RowOut& b, int k, int32_t y) {
+  switch (k & 3) {
+    case 0: b.o0 = y; break;
+    case 1: b.o1 = y; break;
+    case 2: b.o2 = y; break;
+    default:
+      if (b.vec) {
+        *reinterpret_cast<int4*>(b.row + (k - 3)) = make_int4(b.o0, b.o1, b.o2, y);
+      } else {
+        b.row[k - 3] = b.o0;
+        b.row[k - 2] = b.o1;
+        b.row[k - 1] = b.o2;
+        b.row[k] = y;
+      }
+  }
+}
+
+// Write the steps of the current group below k, then -1 at steps k .. l-1.
+__device__ __forceinline__ void row_finish(const RowOut& b, int k, int l) {
+  const int k0 = k & ~3, s = k & 3;
+  if (s > 0) b.row[k0] = b.o0;
+  if (s > 1) b.row[k0 + 1] = b.o1;
+  if (s > 2) b.row[k0 + 2] = b.o2;
+  int kk = k;
+  if (b.vec) {
+    for (; kk < l && (kk & 3); ++kk) b.row[kk] = -1;
+    for (; kk + 4 <= l; kk += 4) *reinterpret_cast<int4*>(b.row + kk) = make_int4(-1, -1, -1, -1);
+  }
+  for (; kk < l; ++kk) b.row[kk] = -1;
 }
 
 // ---------------------------------------------------------------------------
@@ -698,6 +927,92 @@ __device__ __forceinline__ int32_t warp_binned_step(const GraphView& g, bool ali
                                  __shfl_sync(kFull, bt, src), __shfl_sync(kFull, et, src), k,
                                  __shfl_sync(kFull, u, src), a_p, a_q, sm, stream_ratio, lane);
     if (lane == src) x = xx;
+  }
+  return x;
+}
+
+}  // namespace n2v
+
+namespace n2v {
+
+// ---------------------------------------------------------------------------
+// Block tier: the shared-memory queue of the steps a block hands to all four
+// of its warps.
+struct BlockQueue {
+  unsigned long long base;  // first walker of the block's current batch
+  int32_t n[2];             // queued steps, by the parity of the step index
+  BlockScratch scratch;
+  int32_t qt[kPersistThreads], qv[kPersistThreads];  // queued steps: t and v
+  uint64_t qu[kPersistThreads];                      // and their draws
+  int32_t res[kPersistThreads];                      // and their results
+};
+
+// One step for the 128 walkers of a block (one per thread).  As in
+// warp_binned_step, a step whose degrees are all <= thr runs on its own lane
+// and the others run on their warp -- except those whose longer list has at
+// least block_min_deg entries: they are queued in shared memory and taken one
+// after another by the whole block (block_step).  Every thread of the block
+// must call it; it synchronises the block once, twice when the queue is not
+// empty.
+__device__ __forceinline__ int32_t block_binned_step(const GraphView& g, bool alive, int64_t t, int64_t v, int k,
+                                                     uint64_t wid, const WalkJob& J, const LaunchCfg& L, WarpSmem& sm,
+                                                     BlockQueue* bq, int wib, int lane, int tid) {
+  const uint32_t a_p = J.a_p, a_q = J.a_q;
+  int32_t x = -1;
+  bool small = false, big = false;
+  uint64_t u = 0;
+  int64_t bv = 0, ev = 0, bt = 0, et = 0;
+  if (alive) {
+    bv = g.rp[v];
+    ev = g.rp[v + 1];
+    if (k > 0) {
+      bt = g.rp[t];
+      et = g.rp[t + 1];
+    }
+    u = philox_draw(J.seed, wid, (uint32_t)k);
+    if (approx_here(J, k, ev - bv, et - bt)) {
+      small = true;
+      x = static_step(g, bv, ev, u);
+    } else {
+      small = ev - bv <= L.thread_max_deg && (k == 0 || et - bt <= L.thread_max_deg);
+      if (small) x = thread_step(g, t, v, k, u, a_p, a_q);
+      else big = max(ev - bv, et - bt) >= (int64_t)L.block_min_deg;
+    }
+  }
+  unsigned wm = __ballot_sync(kFull, alive && !small && !big);
+  while (wm) {
+    const int src = __ffs(wm) - 1;
+    wm &= wm - 1;
+    const int32_t xx = warp_step(g, __shfl_sync(kFull, t, src), __shfl_sync(kFull, v, src),
+                                 __shfl_sync(kFull, bv, src), __shfl_sync(kFull, ev, src),
+                                 __shfl_sync(kFull, bt, src), __shfl_sync(kFull, et, src), k,
+                                 __shfl_sync(kFull, u, src), a_p, a_q, sm, L.stream_ratio, lane);
+    if (lane == src) x = xx;
+  }
+  const unsigned mb = __ballot_sync(kFull, big);
+  int slot = 0;
+  if (mb) {
+    int b0 = 0;
+    if (lane == 0) b0 = atomicAdd(&bq->n[k & 1], __popc(mb));
+    b0 = __shfl_sync(kFull, b0, 0);
+    if (big) {
+      slot = b0 + __popc(mb & lanemask_lt());
+      bq->qt[slot] = (int32_t)t;
+      bq->qv[slot] = (int32_t)v;
+      bq->qu[slot] = u;
+    }
+  }
+  __syncthreads();
+  const int nq = bq->n[k & 1];
+  if (tid == 0) bq->n[(k + 1) & 1] = 0;  // the next step's counter (nobody touches it before the next barrier)
+  if (nq > 0) {
+    for (int e = 0; e < nq; ++e) {
+      const int32_t y = block_step(g, bq->qt[e], bq->qv[e], k, bq->qu[e], a_p, a_q, sm, &bq->scratch, wib,
+                                   L.stream_ratio, lane);
+      if (tid == 0) bq->res[e] = y;
+    }
+    __syncthreads();
+    if (big) x = bq->res[slot];
   }
   return x;
 }

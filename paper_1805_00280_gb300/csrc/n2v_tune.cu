@@ -1,5 +1,8 @@
 // Autotuner of the persistent sampler: a coordinate descent over its
 // tunables, each candidate timed with CUDA events on a sample of the job.
+// The hub caches (hashed sets and rank bitmaps, the FN-Cache analogue of
+// Section 3.4) are axes too, from none up to the sizes the graph was loaded
+// with.
 // Every tuning gives the same rows (the step is exact on every code path), so
 // only speed is compared.
 #include <stdlib.h>
@@ -94,7 +97,19 @@ int n2v_autotune(n2v_graph* g, const int32_t* starts, int64_t n_starts, int32_t 
   axes.push_back({&n2v_tune::stream_ratio, {15, 40, 100}});
   axes.push_back({&n2v_tune::thread_max_deg, {0, 16, 48}});
   axes.push_back({&n2v_tune::stage_buffers, {2, 4}});
-  if (start.hub_count > 0) axes.push_back({&n2v_tune::hub_count, {0, start.hub_count}});
+  axes.push_back({&n2v_tune::smem_specials, {256, 128, 512}});
+  // the hub caches, up to the sizes the graph was loaded with (its aux holds no more)
+  const n2v_tune& ld = g->tune_loaded;
+  if (ld.bitmap_hubs > 0) {
+    Axis bm{&n2v_tune::bitmap_hubs, {0, ld.bitmap_hubs}};
+    if (ld.bitmap_hubs >= 8) bm.values.push_back(ld.bitmap_hubs / 4);
+    axes.push_back(bm);
+  }
+  if (ld.hub_count > 0) {
+    Axis hb{&n2v_tune::hub_count, {0, ld.hub_count}};
+    if (ld.hub_count >= 64) hb.values.push_back(ld.hub_count / 8);
+    axes.push_back(hb);
+  }
 
   n2v_tune cur = start;
   if (cur.blocks_per_sm <= 0) cur.blocks_per_sm = axes[1].values[0];

@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(kPersistThreads, MINB)
     const int64_t i = (int64_t)base + lane;
     const bool mine = i < J.count;
     const int64_t wid = J.walk_begin + i;
-    int32_t* row = J.walks + i * (int64_t)J.l;
+    RowOut out = row_out(J.walks + i * (int64_t)J.l);
     int64_t t = -1, v = -1;
     bool alive = false;
     if (mine) {
@@ -121,16 +121,12 @@ __global__ void __launch_bounds__(kPersistThreads, MINB)
         atomicOr(J.status, kStInvalidArg);
       }
     }
-    for (int k = 0; k < J.l; ++k) {
-      if (sm.timed_out) break;
-      if (!__any_sync(kFull, alive)) {
-        if (mine)
-          for (int kk = k; kk < J.l; ++kk) row[kk] = -1;
-        break;
-      }
+    int k = 0;
+    for (; k < J.l; ++k) {
+      if (sm.timed_out || !__any_sync(kFull, alive)) break;
       const int32_t x = warp_binned_step(g, alive, t, v, k, (uint64_t)wid, J, L.thread_max_deg, sm, L.stream_ratio,
                                          lane);
-      if (mine) row[k] = alive ? x : -1;
+      if (mine) row_put(out, k, alive ? x : -1);
       if (alive) {
         if (x < 0) {
           alive = false;
@@ -140,6 +136,67 @@ __global__ void __launch_bounds__(kPersistThreads, MINB)
         }
       }
     }
+    if (mine) row_finish(out, k, J.l);  // the last group, and -1 after the walk ended
+  }
+  if (sm.timed_out && lane == 0) atomicOr(J.status, kStTimeout);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent with a block tier: each block takes 128 walkers at a time and
+// advances them together, one step at a time; every step is binned into the
+// lane, warp and block tiers (block_binned_step).  The queue of block-tier
+// steps lives in shared memory after the four warps' areas.
+template <int MINB>
+__global__ void __launch_bounds__(kPersistThreads, MINB)
+    k_persistent_blk(GraphView g, WalkJob J, unsigned long long* __restrict__ counter, LaunchCfg L,
+                     uint32_t* __restrict__ spill) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t gw = (int64_t)blockIdx.x * (kPersistThreads / 32) + warp;
+  WarpSmem sm = warp_smem(smem_raw, warp, L, spill ? spill + gw * (int64_t)L.spill_specials : nullptr);
+  BlockQueue* bq = reinterpret_cast<BlockQueue*>(smem_raw + (size_t)(kPersistThreads / 32) * warp_smem_bytes(L));
+  warp_smem_init(sm, lane);
+  for (;;) {
+    if (tid == 0) {
+      bq->base = atomicAdd(counter, (unsigned long long)kPersistThreads);
+      bq->n[0] = 0;
+      bq->n[1] = 0;
+    }
+    __syncthreads();
+    const int64_t base = (int64_t)bq->base;
+    if (base >= J.count) break;  // uniform: every thread read the same base
+    const int64_t i = base + tid;
+    const bool mine = i < J.count;
+    const int64_t wid = J.walk_begin + i;
+    RowOut out = row_out(J.walks + i * (int64_t)J.l);
+    int64_t t = -1, v = -1;
+    bool alive = false;
+    if (mine) {
+      const int64_t s0 = J.starts[wid % J.n_starts];
+      if (s0 >= 0 && s0 < g.n) {
+        v = s0;
+        alive = true;
+      } else {
+        atomicOr(J.status, kStInvalidArg);
+      }
+    }
+    int k = 0;
+    for (; k < J.l; ++k) {
+      if (sm.timed_out) alive = false;  // a warp whose bounded wait gave up stops its walkers
+      if (!__syncthreads_or(alive)) break;
+      const int32_t x = block_binned_step(g, alive, t, v, k, (uint64_t)wid, J, L, sm, bq, warp, lane, tid);
+      if (mine) row_put(out, k, alive ? x : -1);
+      if (alive) {
+        if (x < 0) {
+          alive = false;
+        } else {
+          t = v;
+          v = x;
+        }
+      }
+    }
+    if (mine) row_finish(out, k, J.l);
+    if (__syncthreads_or(sm.timed_out)) break;  // also: nobody reads bq before thread 0 rewrites it
   }
   if (sm.timed_out && lane == 0) atomicOr(J.status, kStTimeout);
 }
@@ -195,7 +252,9 @@ __global__ void k_selftest_wait(uint32_t* status, long long limit) {
 // ---------------------------------------------------------------------------
 // launch configuration
 
-static int smem_per_block(const LaunchCfg& c) { return (c.block_threads / 32) * warp_smem_bytes(c); }
+static int smem_per_block(const LaunchCfg& c) {
+  return (c.block_threads / 32) * warp_smem_bytes(c) + (c.block_min_deg > 0 ? (int)sizeof(BlockQueue) : 0);
+}
 
 // The persistent kernel is compiled for 4, 5, 6 or 8 resident blocks of 128
 // threads per SM: 128, 96, 80 or 64 registers a thread (each of the SM's four
@@ -204,7 +263,15 @@ static int smem_per_block(const LaunchCfg& c) { return (c.block_threads / 32) * 
 // latency.
 static int persistent_minb(int per_sm) { return per_sm <= 4 ? 4 : per_sm <= 5 ? 5 : per_sm <= 6 ? 6 : 8; }
 
-static const void* persistent_fn(int minb) {
+static const void* persistent_fn(int minb, bool blk) {
+  if (blk) {
+    switch (minb) {
+      case 4: return (const void*)k_persistent_blk<4>;
+      case 6: return (const void*)k_persistent_blk<6>;
+      case 8: return (const void*)k_persistent_blk<8>;
+      default: return (const void*)k_persistent_blk<5>;
+    }
+  }
   switch (minb) {
     case 4: return (const void*)k_persistent<4>;
     case 6: return (const void*)k_persistent<6>;
@@ -215,6 +282,15 @@ static const void* persistent_fn(int minb) {
 
 static void launch_persistent(const LaunchCfg& L, int smem, cudaStream_t s, const GraphView& g, const WalkJob& J,
                               unsigned long long* counter, uint32_t* spill) {
+  if (L.block_min_deg > 0) {
+    switch (L.minb) {
+      case 4: k_persistent_blk<4><<<L.blocks, L.block_threads, smem, s>>>(g, J, counter, L, spill); break;
+      case 6: k_persistent_blk<6><<<L.blocks, L.block_threads, smem, s>>>(g, J, counter, L, spill); break;
+      case 8: k_persistent_blk<8><<<L.blocks, L.block_threads, smem, s>>>(g, J, counter, L, spill); break;
+      default: k_persistent_blk<5><<<L.blocks, L.block_threads, smem, s>>>(g, J, counter, L, spill); break;
+    }
+    return;
+  }
   switch (L.minb) {
     case 4: k_persistent<4><<<L.blocks, L.block_threads, smem, s>>>(g, J, counter, L, spill); break;
     case 6: k_persistent<6><<<L.blocks, L.block_threads, smem, s>>>(g, J, counter, L, spill); break;
@@ -232,14 +308,16 @@ LaunchCfg resolve_launch(const n2v_graph* g, int variant) {
   c.stream_ratio = g->tune.stream_ratio;
   c.spill_specials = g->tune.spill_specials;
   c.stage_buffers = g->tune.stage_buffers;
+  c.block_min_deg = 0;
   if (variant == N2V_PERSISTENT) {
     // 128-thread blocks; the tuning's resident warps per SM (20 by default),
     // as many as shared memory holds
     c.block_threads = kPersistThreads;
+    c.block_min_deg = g->tune.block_min_deg;
     const int warps = g->tune.blocks_per_sm > 0 ? g->tune.blocks_per_sm * (g->tune.block_threads / 32) : 20;
     int per_sm = std::max(1, (warps + 3) / 4);
     const int smem = smem_per_block(c);
-    const void* fn = persistent_fn(8);  // the fewest registers: only shared memory limits it
+    const void* fn = persistent_fn(8, c.block_min_deg > 0);  // the fewest registers: only shared memory limits it
     if (smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, c.block_threads, smem) == cudaSuccess && occ > 0)
@@ -321,7 +399,8 @@ static cudaError_t issue(const n2v_graph* g, const WalkCall& c, cudaStream_t s) 
     return cudaGetLastError();
   }
   // persistent
-  if (smem > 48 * 1024) cudaFuncSetAttribute(persistent_fn(L.minb), cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(persistent_fn(L.minb, L.block_min_deg > 0), cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   const int64_t chunks = n_chunks(g, c.count);
   unsigned long long* counters = (unsigned long long*)c.ws;
   cudaError_t e = cudaMemsetAsync(counters, 0, sizeof(unsigned long long) * (size_t)chunks, s);
@@ -491,6 +570,55 @@ static int walk_impl(const n2v_graph* g, const int32_t* starts, int64_t n_starts
   return issue(g, c, s) == cudaSuccess ? N2V_OK : N2V_ERR_CUDA;
 }
 
+int n2v_walk_stream(const n2v_graph* g, const int32_t* starts, int64_t n_starts, int32_t r, int32_t l, double p,
+                    double q, uint64_t seed, int64_t walk_begin, int64_t walk_count, int32_t* host_walks,
+                    int32_t* dev_ring, int64_t ring_walks, int32_t ring_slots, void* ws, size_t ws_bytes,
+                    int variant, void* stream, void* copy_stream) {
+  if (!g || l < 1 || r < 1 || n_starts < 1 || walk_begin < 0 || walk_count < 0) return N2V_ERR_INVALID_ARG;
+  if (ring_walks < 1 || ring_slots < 1 || ring_slots > 8 || (variant & N2V_FLAG_CUDA_GRAPH)) return N2V_ERR_INVALID_ARG;
+  if (walk_count == 0) return N2V_OK;
+  if (!host_walks || !dev_ring || !starts) return N2V_ERR_INVALID_ARG;
+  if (n_starts > INT64_MAX / r || walk_begin + walk_count > n_starts * (int64_t)r) return N2V_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream, cs = copy_stream ? (cudaStream_t)copy_stream : s;
+  cudaEvent_t ready[8], copied[8];
+  int made = 0, rc = N2V_OK;
+  for (; made < ring_slots; ++made) {
+    if (cudaEventCreateWithFlags(&ready[made], cudaEventDisableTiming) != cudaSuccess) break;
+    if (cudaEventCreateWithFlags(&copied[made], cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventDestroy(ready[made]);
+      break;
+    }
+  }
+  if (made < ring_slots) rc = N2V_ERR_CUDA;
+  const int64_t chunks = (walk_count + ring_walks - 1) / ring_walks;
+  const size_t slot_elems = (size_t)ring_walks * (size_t)l;
+  for (int64_t ci = 0; ci < chunks && rc == N2V_OK; ++ci) {
+    const int b = (int)(ci % ring_slots);
+    const int64_t lo = ci * ring_walks, cnt = std::min<int64_t>(ring_walks, walk_count - lo);
+    int32_t* slot = dev_ring + (size_t)b * slot_elems;
+    // the slot's previous rows must have reached the host before they are overwritten
+    if (ci >= ring_slots && cs != s && cudaStreamWaitEvent(s, copied[b], 0) != cudaSuccess) rc = N2V_ERR_CUDA;
+    if (rc == N2V_OK)
+      rc = n2v_walk(g, starts, n_starts, r, l, p, q, seed, walk_begin + lo, cnt, slot, ws, ws_bytes, variant, stream);
+    if (rc == N2V_OK && cudaEventRecord(ready[b], s) != cudaSuccess) rc = N2V_ERR_CUDA;
+    if (rc == N2V_OK && cs != s && cudaStreamWaitEvent(cs, ready[b], 0) != cudaSuccess) rc = N2V_ERR_CUDA;
+    if (rc == N2V_OK &&
+        cudaMemcpyAsync(host_walks + (size_t)lo * (size_t)l, slot, sizeof(int32_t) * (size_t)cnt * (size_t)l,
+                        cudaMemcpyDeviceToHost, cs) != cudaSuccess)
+      rc = N2V_ERR_CUDA;
+    if (rc == N2V_OK && cudaEventRecord(copied[b], cs) != cudaSuccess) rc = N2V_ERR_CUDA;
+  }
+  // `stream` reaches the end of the call only after the last copies
+  if (rc == N2V_OK && cs != s)
+    for (int64_t ci = std::max<int64_t>(0, chunks - ring_slots); ci < chunks && rc == N2V_OK; ++ci)
+      if (cudaStreamWaitEvent(s, copied[ci % ring_slots], 0) != cudaSuccess) rc = N2V_ERR_CUDA;
+  for (int i = 0; i < made; ++i) {  // released once the work recorded on them completes
+    cudaEventDestroy(ready[i]);
+    cudaEventDestroy(copied[i]);
+  }
+  return rc;
+}
+
 int n2v_walk_traffic(const n2v_graph* g, const int32_t* starts, int64_t n_starts, int64_t walk_begin,
                      int64_t walk_count, int32_t l, const int32_t* walks, uint64_t* out3, void* stream) {
   if (!g || !out3 || l < 1 || n_starts < 1 || walk_begin < 0 || walk_count < 0) return N2V_ERR_INVALID_ARG;
@@ -618,7 +746,8 @@ extern "C" int n2v_walk_noalloc(const n2v_graph* g, const int32_t* starts, int64
 
   LaunchCfg L = resolve_launch(g, N2V_PERSISTENT);
   const int smem = smem_per_block(L);
-  if (smem > 48 * 1024) cudaFuncSetAttribute(persistent_fn(L.minb), cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(persistent_fn(L.minb, L.block_min_deg > 0), cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   // the spill area is whatever the scratch has left, shared evenly by the warps
   const int64_t warps = (int64_t)L.blocks * (L.block_threads / 32);
   const int64_t per_warp = (int64_t)((kNoAllocScratchBytes - kNoAllocCounterBytes) / sizeof(uint32_t)) / warps;

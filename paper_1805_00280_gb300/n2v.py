@@ -48,7 +48,8 @@ class n2v_tune(ctypes.Structure):
                 ("chunk_walkers", ctypes.c_int32), ("hub_budget_mb", ctypes.c_int32),
                 ("stage_window", ctypes.c_int32), ("stream_ratio", ctypes.c_int32),
                 ("spill_specials", ctypes.c_int32), ("stage_buffers", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("bitmap_hubs", ctypes.c_int32), ("block_min_deg", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
@@ -58,7 +59,8 @@ class n2v_graph_info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("weighted", ctypes.c_int32),
                 ("hub_count", ctypes.c_int32), ("max_degree", ctypes.c_int64), ("max_wsum", ctypes.c_uint64),
                 ("hub_min_degree", ctypes.c_int64), ("hub_slots", ctypes.c_int64),
-                ("deg_hist", ctypes.c_int64 * 34), ("w_min", ctypes.c_uint32), ("w_max", ctypes.c_uint32)]
+                ("deg_hist", ctypes.c_int64 * 34), ("w_min", ctypes.c_uint32), ("w_max", ctypes.c_uint32),
+                ("bitmap_hubs", ctypes.c_int32), ("reserved0", ctypes.c_int32), ("bitmap_min_degree", ctypes.c_int64)]
 
 
 class n2v_job(ctypes.Structure):
@@ -105,6 +107,8 @@ def lib() -> ctypes.CDLL:
         L.n2v_walk.argtypes = [vp, vp, i64, i32, i32, dbl, dbl, u64, i64, i64, vp, vp, sz, ctypes.c_int, vp]
         L.n2v_walk_traffic.argtypes = [vp, vp, i64, i64, i64, i32, vp, vp, vp]
         L.n2v_walk_noalloc.argtypes = [vp, vp, i64, i32, i32, dbl, dbl, u64, i64, i64, vp, vp]
+        L.n2v_walk_stream.argtypes = [vp, vp, i64, i32, i32, dbl, dbl, u64, i64, i64, vp, vp, i64, i32, vp, sz,
+                                      ctypes.c_int, vp, vp]
         L.n2v_selftest_timeout.argtypes = [vp, i64, vp]
         L.n2v_walk_approx.argtypes = [vp, vp, i64, i32, i32, dbl, dbl, u64, i64, i64, vp, vp, sz, ctypes.c_int, dbl,
                                       i64, vp]
@@ -232,6 +236,18 @@ def n2v_walk_noalloc(handle: int, starts, n_starts: int, r: int, l: int, p: floa
     rc = lib().n2v_walk_noalloc(handle, _ptr(starts), n_starts, r, l, p, q, seed, walk_begin, walk_count,
                                 _ptr(walks), _stream(stream))
     _check(rc, "n2v_walk_noalloc")
+
+
+def n2v_walk_stream(handle: int, starts, n_starts: int, r: int, l: int, p: float, q: float, seed: int,
+                    walk_begin: int, walk_count: int, host_walks, dev_ring, ring_walks: int, ring_slots: int, ws,
+                    variant: int, stream=None, copy_stream=None) -> None:
+    """Walks in chunks through a device ring, each chunk copied to host memory while the next runs."""
+    ws_bytes = 0 if ws is None else ws.numel() * ws.element_size()
+    cs = None if copy_stream is None else _stream(copy_stream)
+    rc = lib().n2v_walk_stream(handle, _ptr(starts), n_starts, r, l, p, q, seed, walk_begin, walk_count,
+                               _ptr(host_walks), _ptr(dev_ring), ring_walks, ring_slots, _ptr(ws), ws_bytes, variant,
+                               _stream(stream), cs)
+    _check(rc, "n2v_walk_stream")
 
 
 def n2v_walk_traffic(handle: int, starts, n_starts: int, walk_begin: int, walk_count: int, l: int, walks,
@@ -419,6 +435,30 @@ def walk(graph: Graph, starts, r: int, l: int, p: float, q: float, seed: int, va
                         float(approx[0]), int(approx[1]), stream)
     else:
         n2v_walk(graph.handle, starts, n_starts, r, l, p, q, seed, walk_begin, walk_count, out, ws, v, stream)
+    return out
+
+
+def walk_to_host(graph: Graph, starts, r: int, l: int, p: float, q: float, seed: int, ring_walks: int,
+                 ring_slots: int = 2, variant: str | int = "persistent", walk_begin: int = 0,
+                 walk_count: int | None = None, out=None, stream=None, copy_stream=None) -> torch.Tensor:
+    """Walks [walk_count, l] into pinned host memory through a device ring of ring_slots chunks."""
+    dev = graph.row_ptr.device
+    starts = torch.as_tensor(starts, dtype=torch.int32).to(dev).contiguous()
+    n_starts = int(starts.numel())
+    if walk_count is None:
+        walk_count = n_starts * r - walk_begin
+    v = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+    if out is None:
+        out = torch.empty((walk_count, l), dtype=torch.int32).pin_memory()
+    ring = torch.empty((ring_slots, ring_walks, l), dtype=torch.int32, device=dev)
+    need = n2v_walk_ws_bytes(graph.handle, ring_walks, l, v)
+    ws = torch.empty(need // 8 + 32, dtype=torch.int64, device=dev) if need else None
+    if copy_stream is None:
+        copy_stream = torch.cuda.Stream(dev)
+    n2v_walk_stream(graph.handle, starts, n_starts, r, l, p, q, seed, walk_begin, walk_count, out, ring, ring_walks,
+                    ring_slots, ws, v, stream, copy_stream)
+    # the ring and workspace are freed on return: let the call's work finish first
+    torch.cuda.synchronize(dev)
     return out
 
 

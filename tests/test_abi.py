@@ -68,6 +68,10 @@ def test_aux_bytes_sizing():
     t.hub_count = 16
     c = n2v.n2v_graph_aux_bytes(1000, 10_000, False, t)
     assert c - a >= 4 * 1000  # per-vertex hub index
+    t.hub_count = 0
+    t.bitmap_hubs = 8
+    d = n2v.n2v_graph_aux_bytes(1000, 10_000, False, t)
+    assert d - a >= 8 * 16 * ((1000 + 63) // 64)  # 16 bytes per 64 vertices per bitmap hub
     t.reserved[0] = 1
     with pytest.raises(n2v.N2VError):
         n2v.n2v_graph_aux_bytes(1000, 10_000, False, t)
@@ -89,7 +93,8 @@ def test_host_argument_checks_need_no_gpu():
 @pytest.mark.parametrize("field,value", [("block_threads", 512), ("block_threads", 48), ("block_threads", 32),
                                          ("stage_window", 100), ("stage_window", 8192), ("stage_buffers", 3),
                                          ("smem_specials", 48), ("smem_specials", 16), ("stream_ratio", -1),
-                                         ("blocks_per_sm", -1), ("hub_budget_mb", -1)])
+                                         ("blocks_per_sm", -1), ("hub_budget_mb", -1), ("bitmap_hubs", -1),
+                                         ("bitmap_hubs", 4097), ("block_min_deg", -1)])
 def test_tune_validation_rejects(field, value):
     t = n2v.n2v_tune_default()
     setattr(t, field, value)
@@ -98,7 +103,8 @@ def test_tune_validation_rejects(field, value):
 
 
 @pytest.mark.parametrize("field,value", [("block_threads", 64), ("block_threads", 256), ("stage_window", 0),
-                                         ("stage_window", 4096), ("stage_buffers", 4), ("blocks_per_sm", 8)])
+                                         ("stage_window", 4096), ("stage_buffers", 4), ("blocks_per_sm", 8),
+                                         ("bitmap_hubs", 64), ("block_min_deg", 1), ("block_min_deg", 1 << 30)])
 def test_tune_validation_accepts(field, value):
     t = n2v.n2v_tune_default()
     setattr(t, field, value)

@@ -37,6 +37,18 @@ TUNES = {
     "warps16": dict(blocks_per_sm=4),
     "warps24": dict(block_threads=256, blocks_per_sm=3),
     "warps32": dict(blocks_per_sm=8, stage_window=512),
+    # rank bitmaps on every vertex of degree >= 2 (up to 64): the probe modes through one-load lookups
+    "bitmaps": dict(thread_max_deg=0, bitmap_hubs=64, hub_min_degree=2),
+    "bitmaps_segments": dict(thread_max_deg=0, bitmap_hubs=64, hub_min_degree=2, smem_specials=32, spill_specials=0),
+    # the persistent sampler's block batches: every step on the whole block (threshold 1), none (2^30),
+    # and the block tier through each generator and the segment path
+    "block_all": dict(thread_max_deg=0, block_min_deg=1),
+    "block_none": dict(block_min_deg=1 << 30),
+    "block_stage": dict(thread_max_deg=0, block_min_deg=1, stream_ratio=100_000, stage_window=64),
+    "block_probe": dict(thread_max_deg=0, block_min_deg=1, stream_ratio=0),
+    "block_segments": dict(thread_max_deg=0, block_min_deg=1, smem_specials=32, spill_specials=0, stage_window=64,
+                           stream_ratio=100_000),
+    "block_bitmaps": dict(thread_max_deg=0, block_min_deg=1, bitmap_hubs=64, hub_min_degree=2),
 }
 
 
@@ -164,7 +176,9 @@ def test_rmat14_full_output(weighted, pq):
     p, q = pq
     starts = np.arange(g.n, dtype=np.int32)
     want = oracle_rows(g, starts, 20, p, q, 77, np.arange(g.n * 2))
-    for tname in ["default", "hubs", "spill", "probe", "stage", "stage4", "segments", "warps16", "warps24", "warps32"]:
+    for tname in ["default", "hubs", "spill", "probe", "stage", "stage4", "segments", "warps16", "warps24", "warps32",
+                  "bitmaps", "bitmaps_segments", "block_all", "block_none", "block_stage", "block_probe",
+                  "block_segments", "block_bitmaps"]:
         graph = n2v.Graph.from_csr(g, tune=n2v.default_tune(**TUNES[tname]))
         for v in VARIANTS:
             got = gpu_rows(g, starts, 2, 20, p, q, 77, v, graph=graph)
@@ -183,7 +197,7 @@ def sample_ids(g, n_starts, r, k, seed):
 @pytest.fixture(scope="module")
 def rmat20():
     g = G.workload_graph("rmat20")
-    return g, n2v.Graph.from_csr(g, tune=n2v.default_tune(hub_count=1024))
+    return g, n2v.Graph.from_csr(g, tune=n2v.default_tune(hub_count=1024, bitmap_hubs=32))
 
 
 @pytest.mark.parametrize("pq", [(1.0, 1.0), (0.25, 4.0), (4.0, 0.25)])
@@ -211,8 +225,8 @@ def test_rmat23_weighted_workload():
     the hub cache on the top 0.1% of vertices: sampled rows match the oracle."""
     wl = G.WORKLOADS["rmat23w"]
     g = G.workload_graph("rmat23w")
-    graph = n2v.Graph.from_csr(g, tune=n2v.default_tune(hub_count=g.n // 1000))
-    assert graph.info().hub_count > 0
+    graph = n2v.Graph.from_csr(g, tune=n2v.default_tune(hub_count=g.n // 1000, bitmap_hubs=32))
+    assert graph.info().hub_count > 0 and graph.info().bitmap_hubs > 0
     p, q = wl.pq[0]
     starts = np.arange(g.n, dtype=np.int32)
     out = n2v.walk(graph, starts, wl.r, wl.l, p, q, wl.seed, "persistent")
@@ -230,7 +244,8 @@ def test_long_lists_star_and_twin_hubs():
     for g in [big_star(1 << 18), two_hubs(3000, extra=50)]:
         starts = np.arange(min(g.n, 4000), dtype=np.int32)
         want = oracle_rows(g, starts, 5, 0.5, 2.0, 3, np.arange(starts.size))
-        for tname in ["default", "hubs", "spill", "probe", "stage", "stage4", "segments"]:
+        for tname in ["default", "hubs", "spill", "probe", "stage", "stage4", "segments", "bitmaps",
+                      "bitmaps_segments", "block_all", "block_stage", "block_segments", "block_bitmaps"]:
             graph = n2v.Graph.from_csr(g, tune=n2v.default_tune(**TUNES[tname]))
             for v in VARIANTS:
                 got = gpu_rows(g, starts, 1, 5, 0.5, 2.0, 3, v, graph=graph)
