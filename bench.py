@@ -53,6 +53,9 @@ def parse_args():
     ap.add_argument("--pq", default="", help="override (p,q) list, e.g. '1,1;0.25,4'")
     ap.add_argument("--r", type=int, default=0, help="override walks per vertex")
     ap.add_argument("--walk-count", type=int, default=0, help="limit walks per launch (profiling cases)")
+    ap.add_argument("--shuffle-starts", type=int, default=0,
+                    help="start vertices in a seeded random order, so that --walk-count walks start at a uniform "
+                         "sample of the vertices (profiling cases; without it R-MAT's first ids are its hubs)")
     ap.add_argument("--compare-rounds", type=int, default=1,
                     help="the compared variants run the first R rounds (every start vertex R times)")
     ap.add_argument("--compare-walks", type=int, default=0,
@@ -72,12 +75,20 @@ def parse_args():
 
 # workload-specific defaults: the scale-26 graph runs in 8M-walker launches
 # (FN-Multi-style rounds) recorded as one CUDA graph; its compared variants run
-# 2^20 walks in four ranges spread over the job, and the line carries the
-# R-MAT 20 persistent / binned / plain block
+# 2^20 walks in four ranges spread over the job; its end-to-end leg streams the
+# rows to host memory chunk by chunk; and the line carries the R-MAT 20
+# persistent / binned / plain block.  The hub caches are loaded at the sizes
+# given here and the autotuner picks how much of them to use.
 WORKLOAD_DEFAULTS = {
-    "rmat26": {"tune": {"chunk_walkers": 1 << 23}, "cuda_graph": 1, "compare_walks": 1 << 20, "compare_ranges": 4,
-               "c2": 1},
-    "rmat22": {"cuda_graph": 1},
+    # hub caches over the top 0.1% of vertices (2^26 / 1000 hashed sets) and the 64 largest hubs
+    # as rank bitmaps
+    "rmat26": {"tune": {"chunk_walkers": 1 << 23, "bitmap_hubs": 64, "hub_count": 67108, "hub_budget_mb": 16384},
+               "cuda_graph": 1, "compare_walks": 1 << 20, "compare_ranges": 4, "c2": 1, "e2e_stream": 1},
+    "rmat22": {"tune": {"bitmap_hubs": 64, "hub_count": 4194, "hub_budget_mb": 2048}, "cuda_graph": 1},
+    # the hub cache of the top 0.1% of vertices (2^23 / 1000 hashed sets) and 32 rank bitmaps;
+    # the autotuner picks how many of each to keep
+    "rmat23w": {"tune": {"hub_count": 8388, "bitmap_hubs": 32}},
+    "rmat20": {"tune": {"bitmap_hubs": 32}},
 }
 
 
@@ -332,7 +343,10 @@ def run_ours(args):
         # many times over
         n_job = g.n * wl.r
         n_tune = min(1 << 20, n_job)
-        tune_starts = np.resize(np.arange(g.n, dtype=np.int32), n_tune)
+        # the whole job when it has at most 2^20 walks; else 2^20 start vertices drawn at random
+        # (R-MAT's first ids are its hubs: a prefix of the job would over-sample them)
+        tune_starts = np.resize(np.arange(g.n, dtype=np.int32), n_tune) if n_tune == n_job else \
+            np.arange(g.n, dtype=np.int32)
         best, ms = n2v.autotune(graph, tune_starts, wl.l if n_tune == n_job else min(wl.l, 20), pq[0][0], pq[0][1],
                                 wl.seed, sample=n_tune, stream=stream)
         tuned = {"tune": best.as_dict(), "sample_ms": round(ms, 3), "tune_s": round(time.perf_counter() - t0, 2)}
@@ -345,7 +359,10 @@ def run_ours(args):
     r_total, walk_begin, W = shard.weak_shard(world, rank, n_start, r)  # rank k runs rounds [k r, (k+1) r)
     if args.walk_count:
         W = min(W, args.walk_count)
-    starts = torch.arange(n_start, dtype=torch.int32, device=dev)
+    starts_np = np.arange(n_start, dtype=np.int32)
+    if args.shuffle_starts:
+        starts_np = np.random.default_rng(args.shuffle_starts).permutation(n_start).astype(np.int32)
+    starts = torch.from_numpy(starts_np).to(dev)
     outs = [torch.empty((W, l), dtype=torch.int32, device=dev) for _ in pq]
     variant = n2v.VARIANTS[args.variant] | (n2v.N2V_FLAG_CUDA_GRAPH if cuda_graph else 0)
     ws_bytes = max(n2v.n2v_walk_ws_bytes(graph.handle, W, l, variant), 256)
@@ -438,10 +455,17 @@ def run_ours(args):
     # ---- end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
-        starts_h = torch.arange(n_start, dtype=torch.int32).pin_memory()
+        starts_h = torch.from_numpy(starts_np).pin_memory()
         out_h = torch.empty((W, l), dtype=torch.int32).pin_memory()
         starts_d = torch.empty_like(starts)
         K2 = max(1, min(args.steps, 3))
+        streamed = bool(wdef.get("e2e_stream", 0)) and tune.chunk_walkers > 0 and tune.chunk_walkers < W
+        if streamed:
+            # FN-Multi-style output: chunks of chunk_walkers walks into a two-slot device ring, each
+            # chunk copied to the host on a second stream while the next one runs
+            ring_walks = tune.chunk_walkers
+            ring = torch.empty((2, ring_walks, l), dtype=torch.int32, device=dev)
+            copy_stream = torch.cuda.Stream(dev)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         barrier()
         torch.cuda.synchronize(dev)
@@ -450,9 +474,14 @@ def run_ours(args):
             for i in range(len(pq)):
                 starts_d.copy_(starts_h, non_blocking=True)
                 p, q = pq[i]
-                n2v.n2v_walk(graph.handle, starts_d, n_start, r_total, l, p, q, wl.seed, walk_begin, W, outs[i], ws,
-                             variant, stream)
-                out_h.copy_(outs[i], non_blocking=True)
+                if streamed:
+                    n2v.n2v_walk_stream(graph.handle, starts_d, n_start, r_total, l, p, q, wl.seed, walk_begin, W,
+                                        out_h, ring, ring_walks, 2, ws, n2v.VARIANTS[args.variant], stream,
+                                        copy_stream)
+                else:
+                    n2v.n2v_walk(graph.handle, starts_d, n_start, r_total, l, p, q, wl.seed, walk_begin, W, outs[i],
+                                 ws, variant, stream)
+                    out_h.copy_(outs[i], non_blocking=True)
         b.record(stream)
         torch.cuda.synchronize(dev)
         e2e_ms = a.elapsed_time(b)
@@ -460,22 +489,38 @@ def run_ours(args):
             t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             e2e_ms = float(t.item())
+        path = ("pinned host starts -> n2v_walk_stream (chunks of %d walks, 2-slot device ring, each chunk copied "
+                "to pinned host walks while the next runs), per (p,q)" % ring_walks if streamed else
+                "pinned host starts -> n2v_walk -> pinned host walks, per (p,q)")
         e2e = {"value": steps_per_step * K2 / (e2e_ms / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": 4 * n_start * len(pq), "d2h_bytes_per_step": 4 * W * l * len(pq),
-               "steps": K2, "path": "pinned host starts -> n2v_walk -> pinned host walks, per (p,q)"}
-        # SHA-256 of every (p,q) job's full output, through the same host buffer (after the timing)
+               "steps": K2, "path": path}
+        # SHA-256 of every (p,q) job's full output, through the host buffer (after the timing); the
+        # streamed rows must equal the timed device output
         out_sha = []
+        same = True
         for i in range(len(pq)):
-            out_h.copy_(outs[i])
+            if streamed:
+                p, q = pq[i]
+                n2v.n2v_walk_stream(graph.handle, starts_d, n_start, r_total, l, p, q, wl.seed, walk_begin, W, out_h,
+                                    ring, ring_walks, 2, ws, n2v.VARIANTS[args.variant], stream, copy_stream)
+                torch.cuda.synchronize(dev)
+                for c0 in range(0, W, 1 << 22):
+                    same &= bool(torch.equal(out_h[c0:c0 + (1 << 22)].to(dev, non_blocking=False),
+                                             outs[i][c0:c0 + (1 << 22)]))
+            else:
+                out_h.copy_(outs[i])
             out_sha.append(hashlib.sha256(out_h.numpy()).hexdigest())
         e2e["output_sha256"] = out_sha
+        if streamed:
+            e2e["streamed_rows_equal_device_rows"] = same
+            del ring
         del out_h
 
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only)
     cpu = None
     parity = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        starts_np = np.arange(n_start, dtype=np.int32)
         threads = os.cpu_count() or 1
         out_np_cache = {}
 
@@ -500,7 +545,9 @@ def run_ours(args):
         n_rand = sum(desc)
         extra = np.sort(np.random.default_rng(3).choice(W, size=min(max(0, (1 << 14) - n_rand), W), replace=False))
         hubs = np.sort(np.argsort(g.degrees(), kind="stable")[-100:])
-        hub_ids = np.array([k * n_start + h for k in range(W // n_start) for h in hubs], dtype=np.int64)
+        slot_of = np.argsort(starts_np)  # index i of vertex h in starts: walk ids k n + i start at h
+        hub_ids = np.sort(np.array([k * n_start + slot_of[h] for k in range(max(1, W // n_start)) for h in hubs],
+                                   dtype=np.int64))
         hub_ids = hub_ids[hub_ids < W]
         for ids_x in (extra, hub_ids):
             if ids_x.size == 0:
@@ -529,7 +576,8 @@ def run_ours(args):
                    "hubs": info.hub_count, "hub_min_degree": info.hub_min_degree,
                    "max_degree": info.max_degree,
                    "l2": f"flushed between steps ({args.flush_mb} MB write); output {4 * W * l * len(pq) >> 20} MB",
-                   "gen_s": round(gen_s, 2), "load_s": round(load_s, 3)},
+                   "gen_s": round(gen_s, 2), "load_s": round(load_s, 3),
+                   "start_order": f"seeded permutation {args.shuffle_starts}" if args.shuffle_starts else "vertex id"},
         "walks_per_s": W * len(pq) * world * args.steps / (total_ms / 1e3),
         "nominal_steps_per_s": W * l * len(pq) * world * args.steps / (total_ms / 1e3),
         "real_transitions_per_step": steps_per_step,
@@ -608,11 +656,16 @@ def run_serving(args):
     srv = n2v.Server(graph, arena_bytes, cfg, stream)
     counted = torch.zeros((), dtype=torch.int64, device=dev)
 
-    def run_batch(sel, arrivals=None):
-        """Serve jobs `sel`; arrivals[i] = submit time offset (None: all at t=0).
+    copy_stream = torch.cuda.Stream(dev)
+    kept = {}  # job index -> host copy of its rows in the mix (the parity sample)
+
+    def run_batch(sel, arrivals=None, keep_every=0):
+        """Serve jobs `sel`; arrivals[i] = submit time offset (None: all at t=0).  With keep_every,
+        the rows of every keep_every-th job are copied to the host (on a side stream) before release.
         Returns (makespan_s, latencies_s, real transitions)."""
         counted.zero_()
         sub_t, lat = {}, []
+        jid_to_job = {}
         pending = sorted(range(len(sel)), key=lambda i: 0.0 if arrivals is None else arrivals[i])
         pi = 0
         t_start = time.perf_counter()
@@ -623,11 +676,17 @@ def run_serving(args):
                 jb = jobs[sel[pending[pi]]]
                 jid = srv.submit(jb["starts"], jb["l"], jb["p"], jb["q"], jb["seed"])
                 sub_t[jid] = t_start + (0.0 if arrivals is None else arrivals[pending[pi]])
+                jid_to_job[jid] = sel[pending[pi]]
                 pi += 1
             srv.step()
             for jid in srv.poll():
                 lat.append(time.perf_counter() - sub_t[jid])
                 counted.add_((srv.rows(jid) >= 0).sum())
+                jx = jid_to_job[jid]
+                if keep_every and jx % keep_every == 0:
+                    with torch.cuda.stream(copy_stream):  # the job is complete: copy beside the running ticks
+                        kept[jx] = srv.rows(jid).to("cpu", non_blocking=True)
+                    copy_stream.synchronize()
                 srv.release(jid)
                 done += 1
             if pi < len(pending) and arrivals is not None:
@@ -647,9 +706,30 @@ def run_serving(args):
     clocks = ClockSampler(local)
     ticks0 = srv.stats()["ticks"]
     clocks.start()
-    span, lat, steps = run_batch(list(range(len(jobs))), arrivals)
+    span, lat, steps = run_batch(list(range(len(jobs))), arrivals, keep_every=max(1, len(jobs) // 100))
     clk = clocks.stop()
     ticks = srv.stats()["ticks"] - ticks0
+    st = n2v.n2v_stream_status(graph.handle, stream)
+    if st != n2v.N2V_OK:
+        raise RuntimeError(n2v.n2v_strerror(st))
+    # parity of the sampled jobs: the rows each had in the mix equal the same job alone (n2v_walk),
+    # and sampled rows of each equal the oracle's
+    same_alone, oracle_ok, oracle_rows = True, True, 0
+    rng_p = np.random.default_rng(55)
+    for jx, rows_mix in sorted(kept.items()):
+        jb = jobs[jx]
+        alone = n2v.walk(graph, jb["starts"], 1, jb["l"], jb["p"], jb["q"], jb["seed"], "persistent", stream=stream)
+        torch.cuda.synchronize(dev)
+        same_alone &= bool(torch.equal(alone.cpu(), rows_mix))
+        if not args.no_cpu:
+            sel = np.sort(rng_p.choice(jb["size"], size=min(32, jb["size"]), replace=False))
+            want = oracle_mod().walk(g.row_ptr, g.col, None, jb["starts"], jb["l"], jb["p"], jb["q"], jb["seed"], sel,
+                                     threads=os.cpu_count() or 1)
+            oracle_ok &= bool(np.array_equal(rows_mix.numpy()[sel], want))
+            oracle_rows += len(sel)
+        del alone
+    parity = {"jobs_checked": len(kept), "mix_equals_alone": same_alone,
+              "oracle_rows_checked": oracle_rows, "bit_exact": oracle_ok and same_alone}
     st = n2v.n2v_stream_status(graph.handle, stream)
     if st != n2v.N2V_OK:
         raise RuntimeError(n2v.n2v_strerror(st))
@@ -690,6 +770,7 @@ def run_serving(args):
                              "note": "the first jobs one at a time through the plain sampler, no queueing"},
         "gpu_launches": int(ticks),
         "clocks": clk,
+        "parity": parity,
     }
     line["speedup_over_sequential_plain"] = line["value"] / line["sequential_plain"]["value"]
     print(json.dumps(line), flush=True)
@@ -787,7 +868,7 @@ def c2_block(n2v, dev, stream, flush, check_oracle: bool) -> dict:
 
     wl = G.WORKLOADS["rmat20"]
     g = G.workload_graph("rmat20")
-    graph = n2v.Graph.from_csr(g, device=dev)
+    graph = n2v.Graph.from_csr(g, tune=n2v.default_tune(**WORKLOAD_DEFAULTS["rmat20"]["tune"]), device=dev)
     W = g.n  # the first round: walk ids [0, n)
     n2v.autotune(graph, np.arange(g.n, dtype=np.int32), 20, wl.pq[0][0], wl.pq[0][1], wl.seed,
                  sample=min(1 << 20, g.n), stream=stream)

@@ -63,6 +63,10 @@ extern "C" {
 #define N2V_ERR_NO_MEM (-4)        /* a caller buffer is smaller than required       */
 #define N2V_ERR_TIMEOUT (-5)       /* a bounded device wait gave up                  */
 #define N2V_ERR_CUDA (-6)          /* a CUDA runtime call failed                     */
+#define N2V_ERR_INTERNAL (-7)      /* a device self-check failed (checked build only: the
+                                      library compiled with -DN2V_CHECKED verifies positions,
+                                      spill indices, search bounds and stored totals on the
+                                      device and records failures in the status word)   */
 
 /* ---- sampler variants (n2v_walk `variant`) ------------------------------- */
 /* One thread per walker and one launch per step (the plain form). */
@@ -268,8 +272,8 @@ int n2v_walk_traffic(const n2v_graph* g, const int32_t* starts, int64_t n_starts
                      int64_t walk_count, int32_t l, const int32_t* walks, uint64_t* out3, void* stream);
 
 /* Synchronise `stream`, return and clear the device status word of `g`
- * (N2V_OK, N2V_ERR_INVALID_ARG or N2V_ERR_TIMEOUT), or N2V_ERR_CUDA when the
- * stream reports a CUDA error. */
+ * (N2V_OK, N2V_ERR_INVALID_ARG, N2V_ERR_TIMEOUT or, in the checked build,
+ * N2V_ERR_INTERNAL), or N2V_ERR_CUDA when the stream reports a CUDA error. */
 int n2v_stream_status(const n2v_graph* g, void* stream);
 
 /* ---- autotuner -------------------------------------------------------------- */

@@ -20,6 +20,8 @@ REPO = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIBDIR = os.path.join(PKG, "lib")
 LIBN2V = os.path.join(LIBDIR, "libn2v.so")
+# the same sources with the device self-checks compiled in (-DN2V_CHECKED)
+LIBN2V_CHECKED = os.path.join(LIBDIR, "libn2v_checked.so")
 GENDIR = os.path.join(PKG, "graphs")
 LIBGEN = os.path.join(GENDIR, "libn2vgen.so")
 
@@ -75,17 +77,21 @@ def cuda_sources() -> tuple[list[str], list[str]]:
     return cu, hdr
 
 
-def build_n2v(verbose: bool = False, extra_flags: list[str] | None = None) -> str:
-    """Compile every .cu under csrc/ (in parallel) and link libn2v.so."""
+def build_n2v(verbose: bool = False, extra_flags: list[str] | None = None, checked: bool = False) -> str:
+    """Compile every .cu under csrc/ (in parallel) and link libn2v.so (checked: libn2v_checked.so,
+    with the device self-checks)."""
     os.makedirs(LIBDIR, exist_ok=True)
     cu, hdr = cuda_sources()
+    target = LIBN2V_CHECKED if checked else LIBN2V
     flags = ["-O3", "-std=c++17", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
              "-I", os.path.join(REPO, "include"), "-I", CSRC, "--expt-relaxed-constexpr"]
+    if checked:
+        flags.append("-DN2V_CHECKED")
     flags += extra_flags or []
     d = _digest(cu + hdr, " ".join(flags))
-    if _fresh(LIBN2V, d):
-        return LIBN2V
-    objdir = os.path.join(LIBDIR, "obj")
+    if _fresh(target, d):
+        return target
+    objdir = os.path.join(LIBDIR, "obj_checked" if checked else "obj")
     os.makedirs(objdir, exist_ok=True)
 
     def one(src: str) -> str:
@@ -98,17 +104,20 @@ def build_n2v(verbose: bool = False, extra_flags: list[str] | None = None) -> st
 
     with ThreadPoolExecutor(max_workers=max(1, min(len(cu), os.cpu_count() or 1))) as ex:
         objs = list(ex.map(one, cu))
-    link = [NVCC, *ARCH, "-shared", "-o", LIBN2V, *objs, "-lcudart"]
+    link = [NVCC, *ARCH, "-shared", "-o", target, *objs, "-lcudart"]
     if verbose:
         print(" ".join(link), file=sys.stderr)
     _run(link)
-    _stamp(LIBN2V, d)
-    return LIBN2V
+    _stamp(target, d)
+    return target
 
 
 def build_all(verbose: bool = False) -> None:
+    """The generators, then the sampler library and its checked twin, compiled side by side."""
     build_gen(verbose)
-    build_n2v(verbose)
+    with ThreadPoolExecutor(max_workers=2) as ex:
+        for f in [ex.submit(build_n2v, verbose), ex.submit(build_n2v, verbose, None, True)]:
+            f.result()
 
 
 if __name__ == "__main__":

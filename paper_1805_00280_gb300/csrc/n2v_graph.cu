@@ -296,6 +296,7 @@ static int build_hubs(n2v_graph* g, const AuxLayout& L, cudaStream_t s) {
   g->view.hub_off = nullptr;
   g->view.hub_bits = nullptr;
   g->view.hub_slot = nullptr;
+  g->view.hub_min_deg = INT64_MAX;
   g->info.hub_count = 0;
   g->info.hub_min_degree = 0;
   g->info.hub_slots = 0;
@@ -349,6 +350,7 @@ static int build_hubs(n2v_graph* g, const AuxLayout& L, cudaStream_t s) {
   g->view.hub_off = (const int64_t*)(aux + L.hub_off);
   g->view.hub_bits = (const uint32_t*)(aux + L.hub_bits);
   g->view.hub_slot = (const int2*)(aux + L.hub_slot);
+  g->view.hub_min_deg = dstar;
   g->info.hub_count = (int32_t)hubs;
   g->info.hub_min_degree = dstar;
   g->info.hub_slots = slots;
@@ -441,6 +443,7 @@ int n2v_graph_load(const int64_t* row_ptr, const int32_t* col, const uint32_t* w
   g->view.wpre = weighted ? (const uint64_t*)(a + L.wpre) : nullptr;
   g->view.n = n;
   g->view.nnz = nnz;
+  g->view.status = g->status;
 
   int rc = N2V_OK;
   unsigned long long sc[kScWords];

@@ -17,7 +17,21 @@ constexpr unsigned kFull = 0xffffffffu;
 // device status word bits
 constexpr uint32_t kStInvalidArg = 1u;
 constexpr uint32_t kStTimeout = 2u;
-constexpr uint32_t kStInternal = 4u;  // a self-check of the sampler failed
+constexpr uint32_t kStInternal = 4u;  // a self-check of the checked build failed
+
+// Device self-checks of the checked build (compiled with -DN2V_CHECKED):
+// a failed check sets kStInternal in the status word of the graph and the
+// kernel carries on -- no trap, no assert.  Compiled out otherwise.
+#ifdef N2V_CHECKED
+#define N2V_CHECK(g, cond)                                       \
+  do {                                                           \
+    if (!(cond)) atomicOr((g).status, ::n2v::kStInternal);      \
+  } while (0)
+#else
+#define N2V_CHECK(g, cond) \
+  do {                     \
+  } while (0)
+#endif
 
 // Read-only view of a resident graph plus its auxiliary structures.
 struct GraphView {
@@ -32,6 +46,7 @@ struct GraphView {
   const int64_t* __restrict__ hub_off;   // [H] first slot of the hub's table
   const uint32_t* __restrict__ hub_bits; // [H] log2 of the table size
   const int2* __restrict__ hub_slot;     // [slots] (neighbour id or -1 if empty, index in the hub's row)
+  int64_t hub_min_deg;                   // smallest degree of a hub with a hashed set
   // rank bitmaps of the largest hubs (FN-Cache analogue); bm_data null = none.  Entry
   // bm_data[h * bm_words + (x >> 6)] holds bits 64*(x>>6) .. +63 of N(hub h) as a
   // 64-bit mask (.x low, .y high) and in .z the number of neighbours below 64*(x>>6).
@@ -40,6 +55,7 @@ struct GraphView {
   int64_t bm_words;                      // ceil(n / 64)
   int64_t bm_min_deg;                    // smallest degree of a bitmap hub
   uint32_t bm_bits;
+  uint32_t* status;                      // the graph's device status word (self-checks)
 };
 
 // One walk job slice, as every sampler sees it.
@@ -171,6 +187,23 @@ __device__ __forceinline__ int64_t lower_bound_i32(const int32_t* __restrict__ a
 __device__ __forceinline__ bool contains_i32(const int32_t* __restrict__ a, int64_t n, int32_t key) {
   int64_t i = lower_bound_i32(a, n, key);
   return i < n && __ldg(a + i) == key;
+}
+
+// T = sum over N(v) of w(v,x) * alpha(t,x) by a merge over N(v) and N(t) (one
+// lane, O(deg v + deg t)): the checked build recomputes stored totals with it.
+__device__ __forceinline__ uint64_t merge_total(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                                const uint32_t* __restrict__ w, int64_t t, int64_t v, uint32_t a_p,
+                                                uint32_t a_q) {
+  const int64_t bv = rp[v], ev = rp[v + 1], bt = rp[t], et = rp[t + 1];
+  uint64_t T = 0;
+  int64_t pt = bt;
+  for (int64_t j = bv; j < ev; ++j) {
+    const int32_t x = col[j];
+    while (pt < et && col[pt] < x) ++pt;
+    const uint32_t a = (int64_t)x == t ? a_p : ((pt < et && col[pt] == x) ? 65536u : a_q);
+    T += (uint64_t)(w ? w[j] : 1u) * a;
+  }
+  return T;
 }
 
 __device__ __forceinline__ unsigned lanemask_lt() {

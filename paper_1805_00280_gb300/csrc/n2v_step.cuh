@@ -225,6 +225,7 @@ __device__ __forceinline__ void stage_issue(WarpSmem& sm, const GraphView& g, co
   const uint32_t bytes = e16 > a16 ? (uint32_t)(e16 - a16) : 0u;
   const int off = (int)((a - a16) >> 2);
   const int tail0 = bytes ? (int)((e16 - a) >> 2) : 0;  // first element not covered by the copy
+  N2V_CHECK(g, bytes <= (uint32_t)(sm.wlen + 8) * 4u && off + cnt <= sm.wlen + 8 && cnt > 0);
   for (int i = tail0 + lane; i < cnt; i += 32) buf[off + i] = __ldg(src + i);
   __syncwarp();
   if (lane == 0) {
@@ -250,6 +251,7 @@ struct SpecialSink {
   int skip;
   int cap;          // shared-memory slots
   int keep;         // cap + spill slots
+  int lim;          // deg v: positions lie in [0, lim)
 };
 
 __device__ __forceinline__ uint64_t special_delta(const GraphView& g, int64_t bv, int32_t pos, uint32_t cls, uint32_t a_p,
@@ -270,10 +272,15 @@ __device__ __forceinline__ void sink_emit(SpecialSink& k, WarpSmem& sm, const Gr
   if (m2) k.ord_t = k.cnt + __popc(m & ((1u << (__ffs(m2) - 1)) - 1u));
   if (cls) {
     const int ord = k.cnt + __popc(m & lanemask_lt()) - k.skip;
+    N2V_CHECK(g, pos >= 0 && pos < k.lim);
     if (ord >= 0 && ord < k.keep) {
       const uint32_t e = (uint32_t)pos | (cls << 30);
-      if (ord < k.cap) sm.spec[ord] = e;
-      else sm.spill[ord - k.cap] = e;
+      if (ord < k.cap) {
+        sm.spec[ord] = e;
+      } else {
+        N2V_CHECK(g, sm.spill != nullptr && ord - k.cap < sm.spill_cap);
+        sm.spill[ord - k.cap] = e;
+      }
     }
   }
   k.cnt += __popc(m);
@@ -451,6 +458,7 @@ __device__ __forceinline__ void gen_specials(StepCtx& c, int mode, int32_t hub, 
         // fixed-depth searches over the power-of-two window (slots [wcnt, wdepth) hold +inf)
         int lo0, lo1;
         window_rank2_any(wdepth, wbase, key0, key1, lo0, lo1);
+        N2V_CHECK(g, lo0 >= 0 && lo0 <= wcnt && lo1 >= 0 && lo1 <= wcnt && wcnt <= W);
         if (lo0 < wcnt && lds32(wbase + 4u * lo0) < key0) ++lo0;
         if (lo1 < wcnt && lds32(wbase + 4u * lo1) < key1) ++lo1;
         if (go0 && lo0 < wcnt && lds32(wbase + 4u * lo0) == key0) at0 = c.lb + wi * W + lo0;
@@ -510,15 +518,17 @@ __device__ __forceinline__ StepPlan plan_step(StepCtx& c, const GraphView& g, in
   StepPlan pl;
   pl.hub = -1;
   pl.bm = -1;
-  // a longer list with a rank bitmap is always probed: one independent load per candidate
-  if (g.bm_data && longer >= g.bm_min_deg) pl.bm = bm_find(g, (int32_t)(v_short ? t : v));
-  if (pl.bm >= 0) {
+  // a longer list with a rank bitmap or a hashed set is always probed: about one load per
+  // candidate instead of a search
+  const int64_t lv = v_short ? t : v;
+  if (g.bm_data && longer >= g.bm_min_deg) pl.bm = bm_find(g, (int32_t)lv);
+  if (pl.bm < 0 && g.hub_of && longer >= g.hub_min_deg) pl.hub = __ldg(g.hub_of + lv);
+  if (pl.bm >= 0 || pl.hub >= 0) {
     pl.mode = v_short ? 0 : 1;
   } else if (sm.wlen > 0 && longer > 64 && longer * 10 <= (int64_t)stream_ratio * probe_cost) {
     pl.mode = v_short ? 3 : 2;
   } else {
     pl.mode = v_short ? 0 : 1;
-    if (g.hub_of) pl.hub = __ldg(g.hub_of + (v_short ? t : v));
   }
   return pl;
 }
@@ -530,8 +540,9 @@ __device__ __forceinline__ void find_t_slot(StepCtx& c) {
   c.slen = c.dt + (c.has_self ? 0 : 1);
 }
 
-__device__ __forceinline__ SpecialSink new_sink(const WarpSmem& sm) {
+__device__ __forceinline__ SpecialSink new_sink(const WarpSmem& sm, int dv) {
   SpecialSink sk;
+  sk.lim = dv;
   sk.cnt = 0;
   sk.ord_t = -1;
   sk.dpart = 0;
@@ -632,6 +643,13 @@ __device__ __forceinline__ int select_range(StepCtx& c, const StepPlan& pl, Warp
         pos = (int32_t)(e & 0x3fffffffu);
         cls = e >> 30;
       }
+#ifdef N2V_CHECKED
+      {  // kept specials come in strictly increasing position, after the ones already passed
+        const int ppos = __shfl_up_sync(kFull, pos, 1);
+        N2V_CHECK(g, cls == 0u || pos > (lane == 0 ? prev : ppos));
+        N2V_CHECK(g, cls == 0u || pos <= hi_pos);
+      }
+#endif
       const uint64_t dl = special_delta(g, bv, pos, cls, a_p, a_q);
       const uint64_t incl = warp_incl_scan_u64(dl, lane) + D;
       const uint64_t excl = incl - dl;
@@ -675,6 +693,7 @@ __device__ __forceinline__ int select_range(StepCtx& c, const StepPlan& pl, Warp
       chosen = (int)warp_first_above_u64(g.wpre + bv, prev + 1, hi, m, lane);
     }
   }
+  N2V_CHECK(g, chosen > prev0 && chosen <= hi_pos && chosen < c.dv);
   return chosen;
 }
 
@@ -715,7 +734,7 @@ __device__ __forceinline__ int32_t warp_step(const GraphView& g, int64_t t, int6
   const StepPlan pl = plan_step(c, g, t, v, sm, stream_ratio);
   if (pl.mode == 1) find_t_slot(c);  // walks S in order (mode 2 finds t's slot while its copies fly)
   // pass 1: every special (their corrections give T), the first `keep` of them kept
-  SpecialSink sk = new_sink(sm);
+  SpecialSink sk = new_sink(sm, c.dv);
   gen_specials(c, pl.mode, pl.hub, pl.bm, sm, sk, a_p, a_q, lane);
   const uint64_t Wv = static_prefix(g, bv, c.dv - 1);
   const uint64_t T = (uint64_t)a_q * Wv + sink_correction(g, sk, a_p, a_q);
@@ -780,7 +799,7 @@ __device__ __forceinline__ int32_t block_step(const GraphView& g, int64_t t, int
     c.lb = 0;
     c.le = -1;
   }
-  SpecialSink sk = new_sink(sm);
+  SpecialSink sk = new_sink(sm, c.dv);
   if (cb < ce) gen_specials(c, pl.mode, pl.hub, pl.bm, sm, sk, a_p, a_q, lane);
   const uint64_t corr = sink_correction(g, sk, a_p, a_q);
   if (lane == 0) {
@@ -799,6 +818,21 @@ __device__ __forceinline__ int32_t block_step(const GraphView& g, int64_t t, int
     const uint64_t r = scale_draw(u, T);
     const uint64_t C_before = (uint64_t)a_q * static_prefix(g, bv, P_lo - 1) + Dw;
     const uint64_t C_end = (uint64_t)a_q * static_prefix(g, bv, P_hi - 1) + Dw + corr;
+#ifdef N2V_CHECKED
+    {  // exactly one of the four ranges holds the draw, and they tile N(v) in order
+      int claims = 0;
+      uint64_t D = 0;
+      for (int w = 0; w < 4; ++w) {
+        const int lo = bs->pos[w], hi = w < 3 ? bs->pos[w + 1] : c.dv;
+        N2V_CHECK(g, lo <= hi);
+        const uint64_t cb4 = (uint64_t)a_q * static_prefix(g, bv, lo - 1) + D;
+        D += bs->corr[w];
+        const uint64_t ce4 = (uint64_t)a_q * static_prefix(g, bv, hi - 1) + D;
+        claims += (lo < hi && cb4 <= r && r < ce4) ? 1 : 0;
+      }
+      N2V_CHECK(g, claims == 1 && bs->pos[0] == 0);
+    }
+#endif
     if (P_lo < P_hi && C_before <= r && r < C_end) {
       const int j = select_range(c, pl, sm, sk, r, Dw, P_lo - 1, P_hi - 1, a_p, a_q, lane);
       if (lane == 0) bs->result = __ldg(c.nv + j);

@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(256) k_stored_walk(GraphView g, const int64_t*
     if (s0 < 0 || s0 >= g.n) {
       atomicOr(J.status, kStInvalidArg);
     } else {
-      int64_t v = s0, e = -1;
+      int64_t v = s0, e = -1, t = -1;
       for (; k < J.l; ++k) {
         const int64_t bv = __ldg(g.rp + v), dv = __ldg(g.rp + v + 1) - bv;
         if (dv == 0) break;
@@ -218,10 +218,17 @@ __global__ void __launch_bounds__(256) k_stored_walk(GraphView g, const int64_t*
         } else {
           const uint64_t* C = cdf + __ldg(off + e);
           const uint64_t T = __ldg(C + dv - 1);
+          // the edge's stored entries are one per neighbour of v, and its stored total is the on-the-fly one
+          N2V_CHECK(g, __ldg(off + e + 1) - __ldg(off + e) == dv);
+#ifdef N2V_CHECKED
+          N2V_CHECK(g, T == merge_total(g.rp, g.col, g.w, t, v, J.a_p, J.a_q));
+#endif
           if (T == 0) break;
           j = first_above_u64(C, dv, scale_draw(u, T));
         }
+        N2V_CHECK(g, j >= 0 && j < dv);
         e = bv + j;
+        t = v;
         v = __ldg(g.col + e);
         row[k] = (int32_t)v;
       }

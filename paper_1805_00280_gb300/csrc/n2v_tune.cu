@@ -98,6 +98,8 @@ int n2v_autotune(n2v_graph* g, const int32_t* starts, int64_t n_starts, int32_t 
   axes.push_back({&n2v_tune::thread_max_deg, {0, 16, 48}});
   axes.push_back({&n2v_tune::stage_buffers, {2, 4}});
   axes.push_back({&n2v_tune::smem_specials, {256, 128, 512}});
+  // block batches with a block tier for the steps whose longer list is at least this long (0: off)
+  axes.push_back({&n2v_tune::block_min_deg, {0, 4096, 32768}});
   // the hub caches, up to the sizes the graph was loaded with (its aux holds no more)
   const n2v_tune& ld = g->tune_loaded;
   if (ld.bitmap_hubs > 0) {

@@ -126,6 +126,7 @@ __global__ void __launch_bounds__(kPersistThreads, MINB)
       if (sm.timed_out || !__any_sync(kFull, alive)) break;
       const int32_t x = warp_binned_step(g, alive, t, v, k, (uint64_t)wid, J, L.thread_max_deg, sm, L.stream_ratio,
                                          lane);
+      N2V_CHECK(g, !alive || (x >= -1 && x < g.n));
       if (mine) row_put(out, k, alive ? x : -1);
       if (alive) {
         if (x < 0) {
@@ -185,6 +186,7 @@ __global__ void __launch_bounds__(kPersistThreads, MINB)
       if (sm.timed_out) alive = false;  // a warp whose bounded wait gave up stops its walkers
       if (!__syncthreads_or(alive)) break;
       const int32_t x = block_binned_step(g, alive, t, v, k, (uint64_t)wid, J, L, sm, bq, warp, lane, tid);
+      N2V_CHECK(g, !alive || (x >= -1 && x < g.n));
       if (mine) row_put(out, k, alive ? x : -1);
       if (alive) {
         if (x < 0) {
@@ -646,7 +648,7 @@ int n2v_stream_status(const n2v_graph* g, void* stream) {
   if (cudaMemcpy(&st, g->status, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess) return N2V_ERR_CUDA;
   if (st && cudaMemset(g->status, 0, sizeof(st)) != cudaSuccess) return N2V_ERR_CUDA;
   if (st & kStTimeout) return N2V_ERR_TIMEOUT;
-  if (st & kStInternal) return N2V_ERR_CUDA;
+  if (st & kStInternal) return N2V_ERR_INTERNAL;
   if (st & kStInvalidArg) return N2V_ERR_INVALID_ARG;
   return N2V_OK;
 }
@@ -660,6 +662,7 @@ const char* n2v_strerror(int code) {
     case N2V_ERR_NO_MEM: return "caller buffer too small";
     case N2V_ERR_TIMEOUT: return "bounded device wait timed out";
     case N2V_ERR_CUDA: return "CUDA runtime error";
+    case N2V_ERR_INTERNAL: return "a device self-check of the checked build failed";
     default: return "unknown status";
   }
 }

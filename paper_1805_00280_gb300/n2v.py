@@ -26,6 +26,7 @@ N2V_ERR_OVERFLOW = -3
 N2V_ERR_NO_MEM = -4
 N2V_ERR_TIMEOUT = -5
 N2V_ERR_CUDA = -6
+N2V_ERR_INTERNAL = -7
 
 N2V_PLAIN = 0
 N2V_BINNED = 1
@@ -83,13 +84,20 @@ class n2v_serve_stats_t(ctypes.Structure):
 _LIB = None
 
 
+def checked() -> bool:
+    """True when this process uses the checked build (environment N2V_CHECKED=1): the same
+    library with device self-checks that report failures as N2V_ERR_INTERNAL."""
+    return os.environ.get("N2V_CHECKED") == "1"
+
+
 def lib() -> ctypes.CDLL:
-    """Load libn2v.so (building it in-tree when its sources changed)."""
+    """Load libn2v.so, or libn2v_checked.so under N2V_CHECKED=1 (building it in-tree when its
+    sources changed)."""
     global _LIB
     if _LIB is None:
-        path = _build.LIBN2V
+        path = _build.LIBN2V_CHECKED if checked() else _build.LIBN2V
         if not os.path.exists(path) or os.environ.get("N2V_NO_AUTOBUILD") != "1":
-            path = _build.build_n2v()
+            path = _build.build_n2v(checked=checked())
         L = ctypes.CDLL(path)
         vp, i64, i32, u64, dbl, sz = (ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64,
                                       ctypes.c_double, ctypes.c_size_t)

@@ -54,7 +54,7 @@ def test_alpha_q16_rejects(p, q):
 
 
 def test_strerror_covers_codes():
-    for code in range(-6, 1):
+    for code in range(-7, 1):
         assert n2v.n2v_strerror(code) != "unknown status"
     assert n2v.n2v_strerror(42) == "unknown status"
 
