@@ -112,7 +112,11 @@ typedef struct n2v_tune {
                               the persistent sampler advance 128 walkers together, step by step,
                               and a step whose longer list has at least this many entries is
                               taken by the whole block (four warps) instead of one warp      */
-  int32_t reserved[2];     /* must be zero                                                    */
+  int32_t merge_ratio;     /* x10: a step whose two lists both fit a staging window is taken by
+                              a merge of the two lists in shared memory (each lane one segment
+                              of the merge path) when deg v + deg t <= merge_ratio/10 *
+                              32*ceil(short/32) * log2(long); 0 = never                     */
+  int32_t reserved[1];     /* must be zero                                                    */
 } n2v_tune;
 
 /* Fill *t with the library defaults. */

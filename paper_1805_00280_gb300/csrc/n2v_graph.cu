@@ -367,8 +367,8 @@ static bool tune_ok(const n2v_tune& t) {
   if (t.smem_specials % 32) return false;
   if (t.stage_buffers != 2 && t.stage_buffers != 4) return false;
   if (t.bitmap_hubs < 0 || t.bitmap_hubs > 4096 || t.block_min_deg < 0) return false;
-  for (int i = 0; i < 2; ++i)
-    if (t.reserved[i]) return false;
+  if (t.merge_ratio < 0 || t.merge_ratio > 1000000) return false;
+  if (t.reserved[0]) return false;
   return true;
 }
 
@@ -393,6 +393,7 @@ void n2v_tune_default(n2v_tune* t) {
   t->stream_ratio = 40;
   t->spill_specials = 4096;
   t->stage_buffers = 2;
+  t->merge_ratio = 15;
 }
 
 int n2v_graph_aux_bytes(int64_t n, int64_t nnz, int weighted, const n2v_tune* t, size_t* bytes) {

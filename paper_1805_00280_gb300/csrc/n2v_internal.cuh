@@ -91,6 +91,7 @@ struct LaunchCfg {
   int stage_buffers;   // staging windows per warp (2 or 4)
   int minb;            // persistent kernel instance: resident 128-thread blocks per SM it is compiled for
   int block_min_deg;   // persistent sampler: 0 = warps independent; > 0 = block batches with a block tier
+  int merge_ratio;     // x10, merge form of short steps (0: off)
 };
 
 // Shared memory of one warp: four mbarrier slots (32 bytes), the specials

@@ -94,6 +94,7 @@ struct WarpSmem {
   int spill_cap;
   uint32_t parity;   // bit b: parity of the next phase of bar[b]
   bool timed_out;    // a bounded wait gave up
+  int merge_ratio;   // x10: merge both lists when deg v + deg t <= merge_ratio/10 * the probe cost (0: never)
 };
 
 __device__ __forceinline__ WarpSmem warp_smem(unsigned char* base, int warp, const LaunchCfg& L, uint32_t* spill) {
@@ -109,6 +110,7 @@ __device__ __forceinline__ WarpSmem warp_smem(unsigned char* base, int warp, con
   w.spill_cap = spill ? L.spill_specials : 0;
   w.parity = 0;
   w.timed_out = false;
+  w.merge_ratio = L.stage_window > 0 ? L.merge_ratio : 0;
   return w;
 }
 
@@ -208,15 +210,13 @@ __device__ __forceinline__ void window_rank2_any(int depth, uint32_t base, int32
   lo1 = b;
 }
 
-// Fill staging window wi of list L (length llen) into buffer wi % nbuf: the
-// 16-byte-aligned body by one TMA bulk copy, the ragged tail that would read
-// past the 16-byte-aligned end of col by plain loads.
-__device__ __forceinline__ void stage_issue(WarpSmem& sm, const GraphView& g, const int32_t* L, int llen, int wi,
-                                            int lane) {
-  const int b = wi & (sm.nbuf - 1);
+// Fill staging buffer b with src[0, cnt) (0 < cnt <= wlen): the 16-byte-aligned
+// body by one TMA bulk copy, the ragged tail that would read past the
+// 16-byte-aligned end of col by plain loads.  The data starts at element
+// ((uintptr_t)src & 15) / 4 of the buffer; the copy completes on bar[b].
+__device__ __forceinline__ void stage_fill(WarpSmem& sm, const GraphView& g, const int32_t* src, int cnt, int b,
+                                           int lane) {
   int32_t* buf = sm.win + b * (sm.wlen + 8);
-  const int32_t* src = L + wi * sm.wlen;
-  const int cnt = min(sm.wlen, llen - wi * sm.wlen);
   const uintptr_t a = (uintptr_t)src, e = (uintptr_t)(src + cnt);
   const uintptr_t a16 = a & ~(uintptr_t)15;
   uintptr_t e16 = (e + 15) & ~(uintptr_t)15;
@@ -233,6 +233,12 @@ __device__ __forceinline__ void stage_issue(WarpSmem& sm, const GraphView& g, co
     mbar_arrive_expect_tx(&sm.bar[b], bytes);
     if (bytes) bulk_copy_g2s(buf, (const void*)a16, bytes, &sm.bar[b]);
   }
+}
+
+// Fill staging window wi of list L (length llen) into buffer wi % nbuf.
+__device__ __forceinline__ void stage_issue(WarpSmem& sm, const GraphView& g, const int32_t* L, int llen, int wi,
+                                            int lane) {
+  stage_fill(sm, g, L + wi * sm.wlen, min(sm.wlen, llen - wi * sm.wlen), wi & (sm.nbuf - 1), lane);
 }
 
 __device__ __forceinline__ void stage_wait(WarpSmem& sm, int b) {
@@ -501,6 +507,96 @@ __device__ __forceinline__ void gen_specials(StepCtx& c, int mode, int32_t hub, 
   for (int q = wi + 1; q < nwin && q <= wi + sm.nbuf - 1; ++q) stage_wait(sm, q & (sm.nbuf - 1));
 }
 
+// Static prefix W_j = sum of w over N(v) up to position j (W_{-1} = 0).
+__device__ __forceinline__ uint64_t static_prefix(const GraphView& g, int64_t bv, int j) {
+  return j < 0 ? 0ull : (g.w ? __ldg(g.wpre + bv + j) : (uint64_t)(j + 1));
+}
+
+// ---------------------------------------------------------------------------
+// Merge form of a step (k >= 1) whose lists both fit a staging window: N(v)
+// and N(t) land in two shared-memory windows by TMA bulk copies and the warp
+// merges them along the merge path (A = N(v) wins ties): lane k takes the
+// diagonal segment [k (a+b) / 32, (k+1) (a+b) / 32) of the merged order,
+// found by one binary search, and walks it; an element x of N(v) is special
+// when it equals the first unconsumed element of N(t) (x in N(t)) or t.  The
+// per-lane corrections sum (warp scan) to T; the lane whose segment contains
+// the first inclusive prefix above r walks its segment again to find it.
+// Nothing is stored per special: O((deg v + deg t) / 32) per lane.
+__device__ __forceinline__ int32_t merge_step(const StepCtx& c, WarpSmem& sm, uint64_t u, uint32_t a_p, uint32_t a_q,
+                                              int lane) {
+  const GraphView& g = *c.g;
+  const int a = c.dv, b = c.dt;  // 1 <= a, b <= wlen
+  stage_fill(sm, g, c.nv, a, 0, lane);
+  stage_fill(sm, g, c.nt, b, 1, lane);
+  stage_wait(sm, 0);
+  stage_wait(sm, 1);
+  const uint32_t A = smem_addr(sm.win + (((uintptr_t)c.nv & 15) >> 2));
+  const uint32_t B = smem_addr(sm.win + (sm.wlen + 8) + (((uintptr_t)c.nt & 15) >> 2));
+  auto Ald = [&](int i) -> int32_t { return i < a ? lds32(A + 4u * (uint32_t)i) : INT32_MAX; };
+  auto Bld = [&](int j) -> int32_t { return j < b ? lds32(B + 4u * (uint32_t)j) : INT32_MAX; };
+  const int tot = a + b;
+  const int d0 = (int)(((int64_t)lane * tot) >> 5), d1 = (int)(((int64_t)(lane + 1) * tot) >> 5);
+  // merge-path split: A elements among the first d0 of the merged order
+  int lo = max(0, d0 - b), hi = min(d0, a);
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (Ald(mid) <= Bld(d0 - mid - 1)) lo = mid + 1;
+    else hi = mid;
+  }
+  const int i0 = lo, j0 = d0 - lo;
+  const int i1n = __shfl_down_sync(kFull, i0, 1);
+  const int i1 = lane == 31 ? a : i1n;  // first A element of the next segment
+  const int steps = d1 - d0;
+  const uint64_t d1c = (uint64_t)kAlphaOne - (uint64_t)a_q, d2c = (uint64_t)a_p - (uint64_t)a_q;
+  // correction of element x at position i, 0 when not special
+  auto delta = [&](int32_t x, int32_t y, int i) -> uint64_t {
+    if (x == c.t32) return d2c * (g.w ? (uint64_t)__ldg(g.w + c.bv + i) : 1ull);
+    if (x == y) return d1c * (g.w ? (uint64_t)__ldg(g.w + c.bv + i) : 1ull);
+    return 0ull;
+  };
+  uint64_t corr = 0;
+  {
+    int i = i0, j = j0;
+    int32_t av = Ald(i), bv = Bld(j);
+    for (int st = 0; st < steps; ++st) {
+      if (av <= bv) {
+        corr += delta(av, bv, i);
+        av = Ald(++i);
+      } else {
+        bv = Bld(++j);
+      }
+    }
+  }
+  const uint64_t incl = warp_incl_scan_u64(corr, lane);
+  const uint64_t T = (uint64_t)a_q * static_prefix(g, c.bv, a - 1) + __shfl_sync(kFull, incl, 31);
+  if (T == 0) return -1;
+  const uint64_t r = scale_draw(u, T);
+  const uint64_t C_end = (uint64_t)a_q * static_prefix(g, c.bv, i1 - 1) + incl;
+  const unsigned m = __ballot_sync(kFull, C_end > r);  // lane 31's C_end is T > r
+  const int f = __ffs(m) - 1;
+  int chosen = -1;
+  if (lane == f) {
+    uint64_t D = incl - corr;
+    int i = i0, j = j0;
+    int32_t av = Ald(i), bv = Bld(j);
+    for (int st = 0; st < steps; ++st) {
+      if (av <= bv) {
+        D += delta(av, bv, i);
+        if ((uint64_t)a_q * static_prefix(g, c.bv, i) + D > r) {
+          chosen = i;
+          break;
+        }
+        av = Ald(++i);
+      } else {
+        bv = Bld(++j);
+      }
+    }
+  }
+  chosen = __shfl_sync(kFull, chosen, f);
+  N2V_CHECK(g, chosen >= 0 && chosen < a);
+  return lds32(A + 4u * (uint32_t)chosen);
+}
+
 // How a step enumerates its specials (the generator modes of gen_specials) and
 // which hub structure, if any, serves its longer list.
 struct StepPlan {
@@ -510,7 +606,7 @@ struct StepPlan {
 
 // Identical in every lane (and in every warp of a block that shares the step).
 __device__ __forceinline__ StepPlan plan_step(StepCtx& c, const GraphView& g, int64_t t, int64_t v,
-                                              const WarpSmem& sm, int stream_ratio) {
+                                              const WarpSmem& sm, int stream_ratio, int merge_ratio) {
   const bool v_short = c.dv <= c.slen;
   const int shorter = v_short ? c.dv : c.slen;
   const int longer = v_short ? c.dt : c.dv;  // the list that would be staged
@@ -525,6 +621,9 @@ __device__ __forceinline__ StepPlan plan_step(StepCtx& c, const GraphView& g, in
   if (pl.bm < 0 && g.hub_of && longer >= g.hub_min_deg) pl.hub = __ldg(g.hub_of + lv);
   if (pl.bm >= 0 || pl.hub >= 0) {
     pl.mode = v_short ? 0 : 1;
+  } else if (merge_ratio > 0 && c.dv <= sm.wlen && c.dt <= sm.wlen &&
+             (int64_t)(c.dv + c.dt) * 10 <= (int64_t)merge_ratio * probe_cost) {
+    pl.mode = 4;  // both lists fit a window: merge them
   } else if (sm.wlen > 0 && longer > 64 && longer * 10 <= (int64_t)stream_ratio * probe_cost) {
     pl.mode = v_short ? 3 : 2;
   } else {
@@ -558,11 +657,6 @@ __device__ __forceinline__ uint64_t sink_correction(const GraphView& g, const Sp
   if (g.w) return warp_sum_u64(sk.dpart);
   const uint64_t d1 = (uint64_t)kAlphaOne - (uint64_t)a_q, d2 = (uint64_t)a_p - (uint64_t)a_q;
   return (uint64_t)(sk.cnt - (sk.ord_t >= 0 ? 1 : 0)) * d1 + (sk.ord_t >= 0 ? d2 : 0ull);
-}
-
-// Static prefix W_j = sum of w over N(v) up to position j (W_{-1} = 0).
-__device__ __forceinline__ uint64_t static_prefix(const GraphView& g, int64_t bv, int j) {
-  return j < 0 ? 0ull : (g.w ? __ldg(g.wpre + bv + j) : (uint64_t)(j + 1));
 }
 
 // The chosen position, given that it lies in the position range (prev0, hi]
@@ -731,7 +825,8 @@ __device__ __forceinline__ int32_t warp_step(const GraphView& g, int64_t t, int6
     return __ldg(nv + warp_first_above_u64(g.wpre + bv, 0, dv - 1, scale_draw(u, T0), lane));
   }
   StepCtx c = step_ctx(g, t, bv, ev, bt, et);
-  const StepPlan pl = plan_step(c, g, t, v, sm, stream_ratio);
+  const StepPlan pl = plan_step(c, g, t, v, sm, stream_ratio, sm.merge_ratio);
+  if (pl.mode == 4) return merge_step(c, sm, u, a_p, a_q, lane);
   if (pl.mode == 1) find_t_slot(c);  // walks S in order (mode 2 finds t's slot while its copies fly)
   // pass 1: every special (their corrections give T), the first `keep` of them kept
   SpecialSink sk = new_sink(sm, c.dv);
@@ -772,7 +867,8 @@ __device__ __forceinline__ int32_t block_step(const GraphView& g, int64_t t, int
   if (k == 0) return warp_step(g, t, v, bv, ev, 0, 0, 0, u, a_p, a_q, sm, stream_ratio, lane);
   const int64_t bt = g.rp[t], et = g.rp[t + 1];
   StepCtx c = step_ctx(g, t, bv, ev, bt, et);
-  StepPlan pl = plan_step(c, g, t, v, sm, stream_ratio);
+  StepPlan pl = plan_step(c, g, t, v, sm, stream_ratio, sm.merge_ratio);
+  if (pl.mode == 4) return merge_step(c, sm, u, a_p, a_q, lane);  // short lists: every warp merges them alike
   const bool cand_v = pl.mode == 0 || pl.mode == 3;  // candidates: N(v) (positions) or S
   if (!cand_v) find_t_slot(c);
   const int nc = cand_v ? c.dv : c.slen;
@@ -970,35 +1066,37 @@ __device__ __forceinline__ int32_t warp_binned_step(const GraphView& g, bool ali
 namespace n2v {
 
 // ---------------------------------------------------------------------------
-// Block tier: the shared-memory queue of the steps a block hands to all four
-// of its warps.
+// Block tier: the shared-memory queue of one step's work of a block.  Steps
+// for the whole block fill it from the front, steps for one warp from the
+// back; the warps take the latter one at a time, whichever warp is free.
 struct BlockQueue {
   unsigned long long base;  // first walker of the block's current batch
-  int32_t n[2];             // queued steps, by the parity of the step index
+  int32_t nb[2], nw[2];     // queued block steps and warp steps, by the parity of the step index
+  int32_t pull[2];          // warp steps taken so far, by parity
   BlockScratch scratch;
   int32_t qt[kPersistThreads], qv[kPersistThreads];  // queued steps: t and v
   uint64_t qu[kPersistThreads];                      // and their draws
   int32_t res[kPersistThreads];                      // and their results
 };
 
-// One step for the 128 walkers of a block (one per thread).  As in
-// warp_binned_step, a step whose degrees are all <= thr runs on its own lane
-// and the others run on their warp -- except those whose longer list has at
-// least block_min_deg entries: they are queued in shared memory and taken one
-// after another by the whole block (block_step).  Every thread of the block
-// must call it; it synchronises the block once, twice when the queue is not
-// empty.
+// One step for the 128 walkers of a block (one per thread): the degree-binned
+// work queue of the block.  A step whose degrees are all <= thr runs on its own
+// lane.  Every other step is queued in shared memory: those whose longer list
+// has at least block_min_deg entries are taken one after another by the whole
+// block (block_step), the rest one at a time by whichever warp is free
+// (warp_step), so that one costly step does not hold three idle warps.  Every
+// thread of the block must call it; it synchronises the block twice.
 __device__ __forceinline__ int32_t block_binned_step(const GraphView& g, bool alive, int64_t t, int64_t v, int k,
                                                      uint64_t wid, const WalkJob& J, const LaunchCfg& L, WarpSmem& sm,
                                                      BlockQueue* bq, int wib, int lane, int tid) {
   const uint32_t a_p = J.a_p, a_q = J.a_q;
+  const int par = k & 1;
   int32_t x = -1;
-  bool small = false, big = false;
+  bool small = false, big = false, queued = false;
   uint64_t u = 0;
-  int64_t bv = 0, ev = 0, bt = 0, et = 0;
   if (alive) {
-    bv = g.rp[v];
-    ev = g.rp[v + 1];
+    const int64_t bv = g.rp[v], ev = g.rp[v + 1];
+    int64_t bt = 0, et = 0;
     if (k > 0) {
       bt = g.rp[t];
       et = g.rp[t + 1];
@@ -1012,42 +1110,50 @@ __device__ __forceinline__ int32_t block_binned_step(const GraphView& g, bool al
       if (small) x = thread_step(g, t, v, k, u, a_p, a_q);
       else big = max(ev - bv, et - bt) >= (int64_t)L.block_min_deg;
     }
+    queued = !small;
   }
-  unsigned wm = __ballot_sync(kFull, alive && !small && !big);
-  while (wm) {
-    const int src = __ffs(wm) - 1;
-    wm &= wm - 1;
-    const int32_t xx = warp_step(g, __shfl_sync(kFull, t, src), __shfl_sync(kFull, v, src),
-                                 __shfl_sync(kFull, bv, src), __shfl_sync(kFull, ev, src),
-                                 __shfl_sync(kFull, bt, src), __shfl_sync(kFull, et, src), k,
-                                 __shfl_sync(kFull, u, src), a_p, a_q, sm, L.stream_ratio, lane);
-    if (lane == src) x = xx;
+  // queue: block steps at the front, warp steps at the back
+  const unsigned mb = __ballot_sync(kFull, queued && big), mw = __ballot_sync(kFull, queued && !big);
+  int b0 = 0, w0 = 0;
+  if (lane == 0) {
+    if (mb) b0 = atomicAdd(&bq->nb[par], __popc(mb));
+    if (mw) w0 = atomicAdd(&bq->nw[par], __popc(mw));
   }
-  const unsigned mb = __ballot_sync(kFull, big);
-  int slot = 0;
-  if (mb) {
-    int b0 = 0;
-    if (lane == 0) b0 = atomicAdd(&bq->n[k & 1], __popc(mb));
-    b0 = __shfl_sync(kFull, b0, 0);
-    if (big) {
-      slot = b0 + __popc(mb & lanemask_lt());
-      bq->qt[slot] = (int32_t)t;
-      bq->qv[slot] = (int32_t)v;
-      bq->qu[slot] = u;
-    }
+  b0 = __shfl_sync(kFull, b0, 0);
+  w0 = __shfl_sync(kFull, w0, 0);
+  int slot = -1;
+  if (queued) {
+    slot = big ? b0 + __popc(mb & lanemask_lt()) : kPersistThreads - 1 - (w0 + __popc(mw & lanemask_lt()));
+    bq->qt[slot] = (int32_t)t;
+    bq->qv[slot] = (int32_t)v;
+    bq->qu[slot] = u;
   }
   __syncthreads();
-  const int nq = bq->n[k & 1];
-  if (tid == 0) bq->n[(k + 1) & 1] = 0;  // the next step's counter (nobody touches it before the next barrier)
-  if (nq > 0) {
-    for (int e = 0; e < nq; ++e) {
-      const int32_t y = block_step(g, bq->qt[e], bq->qv[e], k, bq->qu[e], a_p, a_q, sm, &bq->scratch, wib,
-                                   L.stream_ratio, lane);
-      if (tid == 0) bq->res[e] = y;
-    }
-    __syncthreads();
-    if (big) x = bq->res[slot];
+  const int nb = bq->nb[par], nw = bq->nw[par];
+  if (tid == 0) {  // the next step's counters (nobody touches them before the next barrier)
+    bq->nb[par ^ 1] = 0;
+    bq->nw[par ^ 1] = 0;
+    bq->pull[par ^ 1] = 0;
   }
+  for (int e = 0; e < nb; ++e) {  // uniform: every thread read the same nb
+    const int32_t y = block_step(g, bq->qt[e], bq->qv[e], k, bq->qu[e], a_p, a_q, sm, &bq->scratch, wib,
+                                 L.stream_ratio, lane);
+    if (tid == 0) bq->res[e] = y;
+  }
+  for (;;) {  // warp steps, one per free warp
+    int e = 0;
+    if (lane == 0) e = atomicAdd(&bq->pull[par], 1);
+    e = __shfl_sync(kFull, e, 0);
+    if (e >= nw) break;
+    const int sl = kPersistThreads - 1 - e;
+    const int64_t qt = bq->qt[sl], qv = bq->qv[sl];
+    const int64_t bv = g.rp[qv], ev = g.rp[qv + 1];
+    const int64_t bt = k > 0 ? g.rp[qt] : 0, et = k > 0 ? g.rp[qt + 1] : 0;
+    const int32_t y = warp_step(g, qt, qv, bv, ev, bt, et, k, bq->qu[sl], a_p, a_q, sm, L.stream_ratio, lane);
+    if (lane == 0) bq->res[sl] = y;
+  }
+  __syncthreads();
+  if (queued) x = bq->res[slot];
   return x;
 }
 

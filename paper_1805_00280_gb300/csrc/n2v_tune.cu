@@ -85,6 +85,20 @@ int n2v_autotune(n2v_graph* g, const int32_t* starts, int64_t n_starts, int32_t 
   };
 
   std::vector<Axis> axes;
+  // the hub caches first (they change which generator most hub steps take), then the rest
+  const n2v_tune& ld = g->tune_loaded;
+  std::vector<Axis> cache_axes;
+  if (ld.hub_count > 0) {
+    Axis hb{&n2v_tune::hub_count, {ld.hub_count, 0}};
+    if (ld.hub_count >= 64) hb.values.push_back(ld.hub_count / 8);
+    cache_axes.push_back(hb);
+  }
+  if (ld.bitmap_hubs > 0) {
+    Axis bm{&n2v_tune::bitmap_hubs, {ld.bitmap_hubs, 0}};
+    if (ld.bitmap_hubs >= 8) bm.values.push_back(ld.bitmap_hubs / 4);
+    cache_axes.push_back(bm);
+  }
+  for (const Axis& ax : cache_axes) axes.push_back(ax);
   axes.push_back({&n2v_tune::stage_window, {512, 1024, 256}});
   {
     const int bw = start.block_threads / 32;
@@ -95,23 +109,14 @@ int n2v_autotune(n2v_graph* g, const int32_t* starts, int64_t n_starts, int32_t 
     axes.push_back(blocks);
   }
   axes.push_back({&n2v_tune::stream_ratio, {15, 40, 100}});
+  axes.push_back({&n2v_tune::merge_ratio, {15, 0, 40}});
   axes.push_back({&n2v_tune::thread_max_deg, {0, 16, 48}});
   axes.push_back({&n2v_tune::stage_buffers, {2, 4}});
   axes.push_back({&n2v_tune::smem_specials, {256, 128, 512}});
   // block batches with a block tier for the steps whose longer list is at least this long (0: off)
-  axes.push_back({&n2v_tune::block_min_deg, {0, 4096, 32768}});
-  // the hub caches, up to the sizes the graph was loaded with (its aux holds no more)
-  const n2v_tune& ld = g->tune_loaded;
-  if (ld.bitmap_hubs > 0) {
-    Axis bm{&n2v_tune::bitmap_hubs, {0, ld.bitmap_hubs}};
-    if (ld.bitmap_hubs >= 8) bm.values.push_back(ld.bitmap_hubs / 4);
-    axes.push_back(bm);
-  }
-  if (ld.hub_count > 0) {
-    Axis hb{&n2v_tune::hub_count, {0, ld.hub_count}};
-    if (ld.hub_count >= 64) hb.values.push_back(ld.hub_count / 8);
-    axes.push_back(hb);
-  }
+  axes.push_back({&n2v_tune::block_min_deg, {0, 1024, 16384}});
+  // and the caches once more, now that the rest has moved (up to the sizes the graph was loaded with)
+  for (const Axis& ax : cache_axes) axes.push_back(ax);
 
   n2v_tune cur = start;
   if (cur.blocks_per_sm <= 0) cur.blocks_per_sm = axes[1].values[0];

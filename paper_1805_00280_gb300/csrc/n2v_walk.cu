@@ -145,8 +145,8 @@ __global__ void __launch_bounds__(kPersistThreads, MINB)
 // ---------------------------------------------------------------------------
 // Persistent with a block tier: each block takes 128 walkers at a time and
 // advances them together, one step at a time; every step is binned into the
-// lane, warp and block tiers (block_binned_step).  The queue of block-tier
-// steps lives in shared memory after the four warps' areas.
+// lane, warp and block tiers through the block's shared-memory work queue
+// (block_binned_step), which lives after the four warps' areas.
 template <int MINB>
 __global__ void __launch_bounds__(kPersistThreads, MINB)
     k_persistent_blk(GraphView g, WalkJob J, unsigned long long* __restrict__ counter, LaunchCfg L,
@@ -160,8 +160,9 @@ __global__ void __launch_bounds__(kPersistThreads, MINB)
   for (;;) {
     if (tid == 0) {
       bq->base = atomicAdd(counter, (unsigned long long)kPersistThreads);
-      bq->n[0] = 0;
-      bq->n[1] = 0;
+      bq->nb[0] = bq->nb[1] = 0;
+      bq->nw[0] = bq->nw[1] = 0;
+      bq->pull[0] = bq->pull[1] = 0;
     }
     __syncthreads();
     const int64_t base = (int64_t)bq->base;
@@ -310,6 +311,7 @@ LaunchCfg resolve_launch(const n2v_graph* g, int variant) {
   c.stream_ratio = g->tune.stream_ratio;
   c.spill_specials = g->tune.spill_specials;
   c.stage_buffers = g->tune.stage_buffers;
+  c.merge_ratio = g->tune.merge_ratio;
   c.block_min_deg = 0;
   if (variant == N2V_PERSISTENT) {
     // 128-thread blocks; the tuning's resident warps per SM (20 by default),

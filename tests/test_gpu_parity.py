@@ -49,6 +49,11 @@ TUNES = {
     "block_segments": dict(thread_max_deg=0, block_min_deg=1, smem_specials=32, spill_specials=0, stage_window=64,
                            stream_ratio=100_000),
     "block_bitmaps": dict(thread_max_deg=0, block_min_deg=1, bitmap_hubs=64, hub_min_degree=2),
+    # the merge form for every step whose lists fit a window (1024, and 64 for ragged windows), and never
+    "merge_all": dict(thread_max_deg=0, merge_ratio=1_000_000),
+    "merge_w64": dict(thread_max_deg=0, merge_ratio=1_000_000, stage_window=64),
+    "merge_off": dict(thread_max_deg=0, merge_ratio=0),
+    "block_merge": dict(thread_max_deg=0, merge_ratio=1_000_000, block_min_deg=1, stage_window=64),
 }
 
 
@@ -178,7 +183,7 @@ def test_rmat14_full_output(weighted, pq):
     want = oracle_rows(g, starts, 20, p, q, 77, np.arange(g.n * 2))
     for tname in ["default", "hubs", "spill", "probe", "stage", "stage4", "segments", "warps16", "warps24", "warps32",
                   "bitmaps", "bitmaps_segments", "block_all", "block_none", "block_stage", "block_probe",
-                  "block_segments", "block_bitmaps"]:
+                  "block_segments", "block_bitmaps", "merge_all", "merge_w64", "merge_off", "block_merge"]:
         graph = n2v.Graph.from_csr(g, tune=n2v.default_tune(**TUNES[tname]))
         for v in VARIANTS:
             got = gpu_rows(g, starts, 2, 20, p, q, 77, v, graph=graph)
@@ -245,7 +250,8 @@ def test_long_lists_star_and_twin_hubs():
         starts = np.arange(min(g.n, 4000), dtype=np.int32)
         want = oracle_rows(g, starts, 5, 0.5, 2.0, 3, np.arange(starts.size))
         for tname in ["default", "hubs", "spill", "probe", "stage", "stage4", "segments", "bitmaps",
-                      "bitmaps_segments", "block_all", "block_stage", "block_segments", "block_bitmaps"]:
+                      "bitmaps_segments", "block_all", "block_stage", "block_segments", "block_bitmaps", "merge_all",
+                      "merge_w64", "block_merge"]:
             graph = n2v.Graph.from_csr(g, tune=n2v.default_tune(**TUNES[tname]))
             for v in VARIANTS:
                 got = gpu_rows(g, starts, 1, 5, 0.5, 2.0, 3, v, graph=graph)
