@@ -522,6 +522,10 @@ __device__ __forceinline__ uint64_t static_prefix(const GraphView& g, int64_t bv
 // per-lane corrections sum (warp scan) to T; the lane whose segment contains
 // the first inclusive prefix above r walks its segment again to find it.
 // Nothing is stored per special: O((deg v + deg t) / 32) per lane.
+__device__ __forceinline__ void sts32(uint32_t addr, int32_t v) {
+  asm volatile("st.shared.s32 [%0], %1;" ::"r"(addr), "r"(v));
+}
+
 __device__ __forceinline__ int32_t merge_step(const StepCtx& c, WarpSmem& sm, uint64_t u, uint32_t a_p, uint32_t a_q,
                                               int lane) {
   const GraphView& g = *c.g;
@@ -532,39 +536,42 @@ __device__ __forceinline__ int32_t merge_step(const StepCtx& c, WarpSmem& sm, ui
   stage_wait(sm, 1);
   const uint32_t A = smem_addr(sm.win + (((uintptr_t)c.nv & 15) >> 2));
   const uint32_t B = smem_addr(sm.win + (sm.wlen + 8) + (((uintptr_t)c.nt & 15) >> 2));
-  auto Ald = [&](int i) -> int32_t { return i < a ? lds32(A + 4u * (uint32_t)i) : INT32_MAX; };
-  auto Bld = [&](int j) -> int32_t { return j < b ? lds32(B + 4u * (uint32_t)j) : INT32_MAX; };
+  // +inf after each list (the windows have slack): the walk needs no bounds tests
+  if (lane == 0) {
+    sts32(A + 4u * (uint32_t)a, INT32_MAX);
+    sts32(B + 4u * (uint32_t)b, INT32_MAX);
+  }
+  __syncwarp();
   const int tot = a + b;
   const int d0 = (int)(((int64_t)lane * tot) >> 5), d1 = (int)(((int64_t)(lane + 1) * tot) >> 5);
   // merge-path split: A elements among the first d0 of the merged order
   int lo = max(0, d0 - b), hi = min(d0, a);
   while (lo < hi) {
     const int mid = (lo + hi) >> 1;
-    if (Ald(mid) <= Bld(d0 - mid - 1)) lo = mid + 1;
+    if (lds32(A + 4u * (uint32_t)mid) <= lds32(B + 4u * (uint32_t)(d0 - mid - 1))) lo = mid + 1;
     else hi = mid;
   }
   const int i0 = lo, j0 = d0 - lo;
   const int i1n = __shfl_down_sync(kFull, i0, 1);
   const int i1 = lane == 31 ? a : i1n;  // first A element of the next segment
-  const int steps = d1 - d0;
   const uint64_t d1c = (uint64_t)kAlphaOne - (uint64_t)a_q, d2c = (uint64_t)a_p - (uint64_t)a_q;
-  // correction of element x at position i, 0 when not special
-  auto delta = [&](int32_t x, int32_t y, int i) -> uint64_t {
-    if (x == c.t32) return d2c * (g.w ? (uint64_t)__ldg(g.w + c.bv + i) : 1ull);
-    if (x == y) return d1c * (g.w ? (uint64_t)__ldg(g.w + c.bv + i) : 1ull);
-    return 0ull;
-  };
   uint64_t corr = 0;
   {
     int i = i0, j = j0;
-    int32_t av = Ald(i), bv = Bld(j);
-    for (int st = 0; st < steps; ++st) {
-      if (av <= bv) {
-        corr += delta(av, bv, i);
-        av = Ald(++i);
+    int32_t av = lds32(A + 4u * (uint32_t)i), bv = lds32(B + 4u * (uint32_t)j);
+    for (int st = d0; st < d1; ++st) {
+      const bool ta = av <= bv;  // the next merged element is A's (ties: A first)
+      const bool sp = ta && (av == c.t32 || av == bv);
+      if (g.w) {
+        if (sp) corr += (av == c.t32 ? d2c : d1c) * (uint64_t)__ldg(g.w + c.bv + i);
       } else {
-        bv = Bld(++j);
+        corr += sp ? (av == c.t32 ? d2c : d1c) : 0ull;
       }
+      i += ta ? 1 : 0;
+      j += ta ? 0 : 1;
+      const int32_t nx = lds32(ta ? A + 4u * (uint32_t)i : B + 4u * (uint32_t)j);
+      av = ta ? nx : av;
+      bv = ta ? bv : nx;
     }
   }
   const uint64_t incl = warp_incl_scan_u64(corr, lane);
@@ -572,27 +579,33 @@ __device__ __forceinline__ int32_t merge_step(const StepCtx& c, WarpSmem& sm, ui
   if (T == 0) return -1;
   const uint64_t r = scale_draw(u, T);
   const uint64_t C_end = (uint64_t)a_q * static_prefix(g, c.bv, i1 - 1) + incl;
-  const unsigned m = __ballot_sync(kFull, C_end > r);  // lane 31's C_end is T > r
-  const int f = __ffs(m) - 1;
+  const int f = __ffs(__ballot_sync(kFull, C_end > r)) - 1;  // lane 31's C_end is T > r
+  // the answer is among positions [p0, p1) of segment f: the warp takes them 32 at a time,
+  // each lane one position (x special when x == t or x is in N(t), by a search of B)
+  const int p0 = __shfl_sync(kFull, i0, f), p1 = __shfl_sync(kFull, i1, f);
+  uint64_t D = __shfl_sync(kFull, incl - corr, f);
   int chosen = -1;
-  if (lane == f) {
-    uint64_t D = incl - corr;
-    int i = i0, j = j0;
-    int32_t av = Ald(i), bv = Bld(j);
-    for (int st = 0; st < steps; ++st) {
-      if (av <= bv) {
-        D += delta(av, bv, i);
-        if ((uint64_t)a_q * static_prefix(g, c.bv, i) + D > r) {
-          chosen = i;
-          break;
-        }
-        av = Ald(++i);
-      } else {
-        bv = Bld(++j);
+  for (int q0 = p0; q0 < p1 && chosen < 0; q0 += 32) {
+    const int p = q0 + lane;
+    uint64_t dl = 0;
+    if (p < p1) {
+      const int32_t x = lds32(A + 4u * (uint32_t)p);
+      int l2 = 0, n2 = b;  // lower bound of x in B
+      while (n2 > 0) {
+        const int h2 = n2 >> 1;
+        const bool lt = lds32(B + 4u * (uint32_t)(l2 + h2)) < x;
+        l2 = lt ? l2 + h2 + 1 : l2;
+        n2 = lt ? n2 - h2 - 1 : h2;
       }
+      const bool sp = x == c.t32 || lds32(B + 4u * (uint32_t)l2) == x;  // B[b] is +inf
+      dl = sp ? (x == c.t32 ? d2c : d1c) * (g.w ? (uint64_t)__ldg(g.w + c.bv + p) : 1ull) : 0ull;
     }
+    const uint64_t inc = warp_incl_scan_u64(dl, lane) + D;
+    const bool hit = p < p1 && (uint64_t)a_q * static_prefix(g, c.bv, p) + inc > r;
+    const unsigned hm = __ballot_sync(kFull, hit);
+    if (hm) chosen = q0 + __ffs(hm) - 1;
+    D = __shfl_sync(kFull, inc, 31);
   }
-  chosen = __shfl_sync(kFull, chosen, f);
   N2V_CHECK(g, chosen >= 0 && chosen < a);
   return lds32(A + 4u * (uint32_t)chosen);
 }
