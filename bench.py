@@ -382,6 +382,8 @@ def run_ours(args):
     if st != n2v.N2V_OK:
         raise RuntimeError(f"sampler status {n2v.n2v_strerror(st)}")
 
+    if n2v.stats_build():
+        n2v.n2v_step_stats(reset=True)  # the stats build counts the timed steps only
     # ---- timed region: K steps, each = every (p,q) job of the workload
     clocks = ClockSampler(local)
     evs = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in pq]
@@ -409,6 +411,7 @@ def run_ours(args):
     st = n2v.n2v_stream_status(graph.handle, stream)
     if st != n2v.N2V_OK:
         raise RuntimeError(f"sampler status {n2v.n2v_strerror(st)}")
+    step_stats = n2v.n2v_step_stats(reset=True) if n2v.stats_build() else None
 
     # ---- work done per step (deterministic rows, so the same every step)
     trans, abytes, lbytes = [], [], []
@@ -592,6 +595,9 @@ def run_ours(args):
         "parity": parity,
         "wall_s_timed": wall,
     }
+    if step_stats is not None:
+        line["step_stats"] = step_stats
+        line["build"] = "stats (per-step counters on: timings are not bench values)"
     if args.sweep:
         line["sweep"] = args.sweep
         line["degree_bins"] = degree_bins(graph, info, outs[0])

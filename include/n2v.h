@@ -393,6 +393,17 @@ int n2v_stored_build(const n2v_graph* g, double p, double q, void* table, size_t
 int n2v_stored_walk(const n2v_graph* g, const void* table, const int32_t* starts, int64_t n_starts, int32_t r,
                     int32_t l, uint64_t seed, int64_t walk_begin, int64_t walk_count, int32_t* walks, void* stream);
 
+/* Step statistics of the stats build (the library compiled with
+ * -DN2V_STATS; the paper has no counterpart): out[0..n) receives, summed over
+ * every sampler launch since the last reset, per kind of step the number of
+ * steps, the SM clock cycles lane 0 of the warp spent in them and the lengths
+ * of their shorter and longer lists (layout: lane-tier batches and cycles,
+ * first steps and cycles, then four words per generator mode 0..4, then
+ * segment re-enumerations, spilled steps and the warps' total cycles in the
+ * persistent loop).  Synchronises the device; reset != 0 zeroes the counters.
+ * Other builds fill out with zeros and return N2V_ERR_INVALID_ARG.  n <= 32. */
+int n2v_step_stats(uint64_t* out, int32_t n, int32_t reset);
+
 /* Number of SMs and the persistent grid the handle would launch: blocks of
  * 128 threads, as many per SM as the tuning's resident warps ask for (20 by
  * default) and shared memory holds. */

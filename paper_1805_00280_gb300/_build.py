@@ -20,8 +20,10 @@ REPO = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIBDIR = os.path.join(PKG, "lib")
 LIBN2V = os.path.join(LIBDIR, "libn2v.so")
-# the same sources with the device self-checks compiled in (-DN2V_CHECKED)
+# the same sources with the device self-checks compiled in (-DN2V_CHECKED), and with the
+# step statistics (-DN2V_STATS)
 LIBN2V_CHECKED = os.path.join(LIBDIR, "libn2v_checked.so")
+LIBN2V_STATS = os.path.join(LIBDIR, "libn2v_stats.so")
 GENDIR = os.path.join(PKG, "graphs")
 LIBGEN = os.path.join(GENDIR, "libn2vgen.so")
 
@@ -77,21 +79,24 @@ def cuda_sources() -> tuple[list[str], list[str]]:
     return cu, hdr
 
 
-def build_n2v(verbose: bool = False, extra_flags: list[str] | None = None, checked: bool = False) -> str:
+def build_n2v(verbose: bool = False, extra_flags: list[str] | None = None, checked: bool = False,
+              stats: bool = False) -> str:
     """Compile every .cu under csrc/ (in parallel) and link libn2v.so (checked: libn2v_checked.so,
-    with the device self-checks)."""
+    with the device self-checks; stats: libn2v_stats.so, with the step statistics)."""
     os.makedirs(LIBDIR, exist_ok=True)
     cu, hdr = cuda_sources()
-    target = LIBN2V_CHECKED if checked else LIBN2V
+    target = LIBN2V_CHECKED if checked else (LIBN2V_STATS if stats else LIBN2V)
     flags = ["-O3", "-std=c++17", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
              "-I", os.path.join(REPO, "include"), "-I", CSRC, "--expt-relaxed-constexpr"]
     if checked:
         flags.append("-DN2V_CHECKED")
+    if stats:
+        flags.append("-DN2V_STATS")
     flags += extra_flags or []
     d = _digest(cu + hdr, " ".join(flags))
     if _fresh(target, d):
         return target
-    objdir = os.path.join(LIBDIR, "obj_checked" if checked else "obj")
+    objdir = os.path.join(LIBDIR, "obj_checked" if checked else ("obj_stats" if stats else "obj"))
     os.makedirs(objdir, exist_ok=True)
 
     def one(src: str) -> str:
@@ -113,10 +118,11 @@ def build_n2v(verbose: bool = False, extra_flags: list[str] | None = None, check
 
 
 def build_all(verbose: bool = False) -> None:
-    """The generators, then the sampler library and its checked twin, compiled side by side."""
+    """The generators, then the sampler library and its checked and stats twins, compiled side by side."""
     build_gen(verbose)
-    with ThreadPoolExecutor(max_workers=2) as ex:
-        for f in [ex.submit(build_n2v, verbose), ex.submit(build_n2v, verbose, None, True)]:
+    with ThreadPoolExecutor(max_workers=3) as ex:
+        for f in [ex.submit(build_n2v, verbose), ex.submit(build_n2v, verbose, None, True),
+                  ex.submit(build_n2v, verbose, None, False, True)]:
             f.result()
 
 

@@ -393,7 +393,7 @@ void n2v_tune_default(n2v_tune* t) {
   t->stream_ratio = 40;
   t->spill_specials = 4096;
   t->stage_buffers = 2;
-  t->merge_ratio = 5;
+  t->merge_ratio = 0;
 }
 
 int n2v_graph_aux_bytes(int64_t n, int64_t nnz, int weighted, const n2v_tune* t, size_t* bytes) {

@@ -33,6 +33,30 @@ constexpr uint32_t kStInternal = 4u;  // a self-check of the checked build faile
   } while (0)
 #endif
 
+// Step statistics of the stats build (compiled with -DN2V_STATS): lane 0 of a
+// warp adds counts, SM clock cycles and list lengths per kind of step to a
+// device array that n2v_step_stats reads.  Compiled out otherwise.
+enum : int {
+  kStatLaneSteps = 0,    // warp-batches of lane-tier work, and their cycles
+  kStatLaneCycles = 1,
+  kStatFirst = 2,        // first steps (k = 0) on a warp, and cycles
+  kStatFirstCycles = 3,
+  kStatMode = 4,         // + 4m: warp steps of generator mode m (0..4), cycles, shorter and longer lengths
+  kStatSegments = 24,    // re-enumerations of a step's specials (segments beyond the first)
+  kStatSpilled = 25,     // steps whose specials overflowed shared memory
+  kStatKernelCycles = 26,  // sum over warps of their time in the persistent loop
+  kStatWords = 32
+};
+#ifdef N2V_STATS
+// one array per translation unit (no relocatable device code); n2v_step_stats reads the samplers'
+static __device__ unsigned long long g_step_stats[kStatWords];
+#define N2V_STAT(i, x) atomicAdd(&::n2v::g_step_stats[(i)], (unsigned long long)(x))
+#else
+#define N2V_STAT(i, x) \
+  do {                  \
+  } while (0)
+#endif
+
 // Read-only view of a resident graph plus its auxiliary structures.
 struct GraphView {
   const int64_t* __restrict__ rp;      // [n+1]

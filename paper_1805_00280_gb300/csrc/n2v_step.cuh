@@ -95,7 +95,23 @@ struct WarpSmem {
   uint32_t parity;   // bit b: parity of the next phase of bar[b]
   bool timed_out;    // a bounded wait gave up
   int merge_ratio;   // x10: merge both lists when deg v + deg t <= merge_ratio/10 * the probe cost (0: never)
+  uint32_t inv_q;    // the a_q that aq_inv belongs to (0: none yet)
+  uint64_t aq_inv;   // floor((2^64 - 1) / inv_q)
 };
+
+// floor(x / d) for d = sm.inv_q, by a multiply with the cached reciprocal
+// floor((2^64 - 1) / d): the estimate umulhi(x, inv) is floor(x / d) or one
+// less, and one comparison corrects it.  The reciprocal is computed once per
+// warp and value of d (uniform in the warp).
+__device__ __forceinline__ uint64_t div_aq(WarpSmem& sm, uint64_t x, uint32_t d) {
+  if (sm.inv_q != d) {
+    sm.inv_q = d;
+    sm.aq_inv = ~0ull / (uint64_t)d;
+  }
+  uint64_t q = __umul64hi(x, sm.aq_inv);
+  if (x - q * (uint64_t)d >= (uint64_t)d) ++q;
+  return q;
+}
 
 __device__ __forceinline__ WarpSmem warp_smem(unsigned char* base, int warp, const LaunchCfg& L, uint32_t* spill) {
   WarpSmem w;
@@ -111,6 +127,8 @@ __device__ __forceinline__ WarpSmem warp_smem(unsigned char* base, int warp, con
   w.parity = 0;
   w.timed_out = false;
   w.merge_ratio = L.stage_window > 0 ? L.merge_ratio : 0;
+  w.inv_q = 0;
+  w.aq_inv = 0;
   return w;
 }
 
@@ -689,6 +707,7 @@ __device__ __forceinline__ int select_range(StepCtx& c, const StepPlan& pl, Warp
   const uint64_t d1 = (uint64_t)kAlphaOne - (uint64_t)a_q, d2 = (uint64_t)a_p - (uint64_t)a_q;
   for (int seg = 0;; seg += sk.keep) {
     if (seg > 0) {
+      if (lane == 0) N2V_STAT(kStatSegments, 1);
       sk.cnt = 0;
       sk.ord_t = -1;
       sk.skip = seg;
@@ -792,7 +811,7 @@ __device__ __forceinline__ int select_range(StepCtx& c, const StepPlan& pl, Warp
   if (!found) {
     // first j in (prev, hi] with a_q * W_j + D > r
     const int hi = chosen >= 0 ? chosen : hi_pos;
-    const uint64_t m = (r - D) / (uint64_t)a_q;
+    const uint64_t m = div_aq(sm, r - D, a_q);
     if (!g.w) {
       chosen = m > (uint64_t)hi ? hi : (int)m;
       if (chosen <= prev) chosen = prev + 1;
@@ -837,9 +856,29 @@ __device__ __forceinline__ int32_t warp_step(const GraphView& g, int64_t t, int6
     if (T0 == 0) return -1;
     return __ldg(nv + warp_first_above_u64(g.wpre + bv, 0, dv - 1, scale_draw(u, T0), lane));
   }
+#ifdef N2V_STATS
+  const long long t_enter = clock64();
+#endif
   StepCtx c = step_ctx(g, t, bv, ev, bt, et);
   const StepPlan pl = plan_step(c, g, t, v, sm, stream_ratio, sm.merge_ratio);
-  if (pl.mode == 4) return merge_step(c, sm, u, a_p, a_q, lane);
+#ifdef N2V_STATS
+  auto stat = [&]() {
+    if (lane == 0) {
+      const int sh = c.dv <= c.dt + 1 ? c.dv : c.dt + 1, lg = c.dv <= c.dt + 1 ? c.dt : c.dv;
+      N2V_STAT(kStatMode + 4 * pl.mode, 1);
+      N2V_STAT(kStatMode + 4 * pl.mode + 1, clock64() - t_enter);
+      N2V_STAT(kStatMode + 4 * pl.mode + 2, sh);
+      N2V_STAT(kStatMode + 4 * pl.mode + 3, lg);
+    }
+  };
+#endif
+  if (pl.mode == 4) {
+    const int32_t x = merge_step(c, sm, u, a_p, a_q, lane);
+#ifdef N2V_STATS
+    stat();
+#endif
+    return x;
+  }
   if (pl.mode == 1) find_t_slot(c);  // walks S in order (mode 2 finds t's slot while its copies fly)
   // pass 1: every special (their corrections give T), the first `keep` of them kept
   SpecialSink sk = new_sink(sm, c.dv);
@@ -847,8 +886,12 @@ __device__ __forceinline__ int32_t warp_step(const GraphView& g, int64_t t, int6
   const uint64_t Wv = static_prefix(g, bv, c.dv - 1);
   const uint64_t T = (uint64_t)a_q * Wv + sink_correction(g, sk, a_p, a_q);
   if (T == 0) return -1;
+  if (lane == 0 && sk.cnt > sk.cap) N2V_STAT(kStatSpilled, 1);
   const int chosen = select_range(c, pl, sm, sk, scale_draw(u, T), 0ull, -1, c.dv - 1, a_p, a_q, lane);
   __syncwarp();
+#ifdef N2V_STATS
+  stat();
+#endif
   return __ldg(nv + chosen);
 }
 
@@ -1044,6 +1087,9 @@ __device__ __forceinline__ int32_t warp_binned_step(const GraphView& g, bool ali
   bool small = false;
   uint64_t u = 0;
   int64_t bv = 0, ev = 0, bt = 0, et = 0;
+#ifdef N2V_STATS
+  const long long t_lane = clock64();
+#endif
   if (alive) {
     // every lane fetches its own walker's row bounds: 32 independent loads
     bv = g.rp[v];
@@ -1062,6 +1108,16 @@ __device__ __forceinline__ int32_t warp_binned_step(const GraphView& g, bool ali
     }
   }
   unsigned wm = __ballot_sync(kFull, alive && !small);
+#ifdef N2V_STATS
+  {
+    const long long dt_lane = clock64() - t_lane;
+    const long long mx = __reduce_max_sync(kFull, (unsigned)min(dt_lane, (long long)0xffffffff));
+    if (lane == 0 && __any_sync(kFull, alive)) {
+      N2V_STAT(k == 0 ? kStatFirst : kStatLaneSteps, 1);
+      N2V_STAT(k == 0 ? kStatFirstCycles : kStatLaneCycles, mx);
+    }
+  }
+#endif
   while (wm) {
     const int src = __ffs(wm) - 1;
     wm &= wm - 1;

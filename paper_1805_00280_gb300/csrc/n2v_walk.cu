@@ -101,6 +101,9 @@ __global__ void __launch_bounds__(kPersistThreads, MINB)
   const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
   WarpSmem sm = warp_smem(smem_raw, warp, L, spill ? spill + gw * (int64_t)L.spill_specials : nullptr);
   warp_smem_init(sm, lane);
+#ifdef N2V_STATS
+  const long long t_kernel = clock64();
+#endif
   while (!sm.timed_out) {
     unsigned long long base = 0;
     if (lane == 0) base = atomicAdd(counter, 32ull);
@@ -139,6 +142,9 @@ __global__ void __launch_bounds__(kPersistThreads, MINB)
     }
     if (mine) row_finish(out, k, J.l);  // the last group, and -1 after the walk ended
   }
+#ifdef N2V_STATS
+  if (lane == 0) N2V_STAT(kStatKernelCycles, clock64() - t_kernel);
+#endif
   if (sm.timed_out && lane == 0) atomicOr(J.status, kStTimeout);
 }
 
@@ -667,6 +673,23 @@ const char* n2v_strerror(int code) {
     case N2V_ERR_INTERNAL: return "a device self-check of the checked build failed";
     default: return "unknown status";
   }
+}
+
+int n2v_step_stats(uint64_t* out, int32_t n, int32_t reset) {
+  if (!out || n < 1 || n > kStatWords) return N2V_ERR_INVALID_ARG;
+#ifdef N2V_STATS
+  if (cudaDeviceSynchronize() != cudaSuccess) return N2V_ERR_CUDA;
+  if (cudaMemcpyFromSymbol(out, g_step_stats, sizeof(uint64_t) * (size_t)n) != cudaSuccess) return N2V_ERR_CUDA;
+  if (reset) {
+    static const unsigned long long zero[kStatWords] = {};
+    if (cudaMemcpyToSymbol(g_step_stats, zero, sizeof(zero)) != cudaSuccess) return N2V_ERR_CUDA;
+  }
+  return N2V_OK;
+#else
+  (void)reset;
+  memset(out, 0, sizeof(uint64_t) * (size_t)n);
+  return N2V_ERR_INVALID_ARG;  // not the stats build
+#endif
 }
 
 int n2v_launch_shape(const n2v_graph* g, int32_t* sms, int32_t* blocks, int32_t* threads) {

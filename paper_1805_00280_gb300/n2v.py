@@ -90,14 +90,20 @@ def checked() -> bool:
     return os.environ.get("N2V_CHECKED") == "1"
 
 
+def stats_build() -> bool:
+    """True when this process uses the stats build (environment N2V_STATS=1): the same library
+    with per-kind step counters that n2v_step_stats reads."""
+    return os.environ.get("N2V_STATS") == "1"
+
+
 def lib() -> ctypes.CDLL:
-    """Load libn2v.so, or libn2v_checked.so under N2V_CHECKED=1 (building it in-tree when its
-    sources changed)."""
+    """Load libn2v.so, or libn2v_checked.so under N2V_CHECKED=1, or libn2v_stats.so under
+    N2V_STATS=1 (building it in-tree when its sources changed)."""
     global _LIB
     if _LIB is None:
-        path = _build.LIBN2V_CHECKED if checked() else _build.LIBN2V
+        path = _build.LIBN2V_CHECKED if checked() else (_build.LIBN2V_STATS if stats_build() else _build.LIBN2V)
         if not os.path.exists(path) or os.environ.get("N2V_NO_AUTOBUILD") != "1":
-            path = _build.build_n2v(checked=checked())
+            path = _build.build_n2v(checked=checked(), stats=stats_build() and not checked())
         L = ctypes.CDLL(path)
         vp, i64, i32, u64, dbl, sz = (ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64,
                                       ctypes.c_double, ctypes.c_size_t)
@@ -124,6 +130,7 @@ def lib() -> ctypes.CDLL:
         L.n2v_strerror.argtypes = [ctypes.c_int]
         L.n2v_strerror.restype = ctypes.c_char_p
         L.n2v_launch_shape.argtypes = [vp, P(i32), P(i32), P(i32)]
+        L.n2v_step_stats.argtypes = [vp, i32, i32]
         L.n2v_serve_cfg_default.argtypes = [P(n2v_serve_cfg)]
         L.n2v_serve_cfg_default.restype = None
         L.n2v_serve_create.argtypes = [vp, vp, sz, P(n2v_serve_cfg), vp, P(vp)]
@@ -276,6 +283,20 @@ def n2v_launch_shape(handle: int) -> tuple[int, int, int]:
     a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
     _check(lib().n2v_launch_shape(handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "n2v_launch_shape")
     return a.value, b.value, c.value
+
+
+STAT_NAMES = (["lane_batches", "lane_cycles", "first_batches", "first_cycles"] +
+              [f"mode{m}_{f}" for m in range(5) for f in ("steps", "cycles", "short_sum", "long_sum")] +
+              ["segments", "spilled_steps", "kernel_warp_cycles"])
+
+
+def n2v_step_stats(reset: bool = True) -> dict | None:
+    """Step statistics of the stats build as a dict (None in other builds)."""
+    out = np.zeros(32, dtype=np.uint64)
+    rc = lib().n2v_step_stats(out.ctypes.data, 32, int(reset))
+    if rc != N2V_OK:
+        return None
+    return {name: int(out[i]) for i, name in enumerate(STAT_NAMES)}
 
 
 def n2v_autotune_ws_bytes(handle: int, sample: int, l: int) -> int:
