@@ -1112,7 +1112,8 @@ __device__ __forceinline__ int32_t warp_binned_step(const GraphView& g, bool ali
   {
     const long long dt_lane = clock64() - t_lane;
     const long long mx = __reduce_max_sync(kFull, (unsigned)min(dt_lane, (long long)0xffffffff));
-    if (lane == 0 && __any_sync(kFull, alive)) {
+    const bool any_alive = __any_sync(kFull, alive);  // every lane votes (never inside a lane branch)
+    if (lane == 0 && any_alive) {
       N2V_STAT(k == 0 ? kStatFirst : kStatLaneSteps, 1);
       N2V_STAT(k == 0 ? kStatFirstCycles : kStatLaneCycles, mx);
     }

@@ -122,3 +122,16 @@ def test_stored_serve_and_tuner_host_checks_need_no_gpu():
     assert L.n2v_serve_create(None, None, 0, None, None, ctypes.byref(srv)) == n2v.N2V_ERR_INVALID_ARG
     assert L.n2v_autotune_ws_bytes(None, 1, 1, ctypes.byref(b)) == n2v.N2V_ERR_INVALID_ARG
     assert L.n2v_walk_traffic(None, None, 1, 0, 0, 1, None, None, None) == n2v.N2V_ERR_INVALID_ARG
+
+
+def test_step_stats_report_nothing_outside_the_stats_build():
+    """n2v_step_stats is a stats-build tool: the product library fills zeros and says so, without a device."""
+    import numpy as np
+
+    L = n2v.lib()
+    out = np.full(32, 7, dtype=np.uint64)
+    assert L.n2v_step_stats(out.ctypes.data, 33, 0) == n2v.N2V_ERR_INVALID_ARG
+    if not n2v.stats_build():
+        assert L.n2v_step_stats(out.ctypes.data, 32, 0) == n2v.N2V_ERR_INVALID_ARG
+        assert not out.any()
+        assert n2v.n2v_step_stats() is None
