@@ -45,6 +45,11 @@ enum : int {
   kStatSegments = 24,    // re-enumerations of a step's specials (segments beyond the first)
   kStatSpilled = 25,     // steps whose specials overflowed shared memory
   kStatKernelCycles = 26,  // sum over warps of their time in the persistent loop
+  kStatGenCycles = 27,     // staged steps: cycles of the first enumeration of the specials
+  kStatSelCycles = 28,     // staged steps: cycles of the selection (including re-enumerations)
+  kStatChunks = 29,        // staged steps: chunks of 64 keys
+  kStatWindows = 30,       // staged steps: windows landed
+  kStatSearches = 31,      // staged steps: window searches (a chunk's keys in one window)
   kStatWords = 32
 };
 #ifdef N2V_STATS

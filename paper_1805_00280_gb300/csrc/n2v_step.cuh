@@ -434,15 +434,18 @@ __device__ __forceinline__ void gen_specials(StepCtx& c, int mode, int32_t hub, 
   auto key_at = [&](int i) -> int32_t { return i < nkeys ? (stage_v ? s_at(c, i) : __ldg(c.nv + i)) : 0; };
   // search depth of a window holding cnt elements: the next power of two
   auto depth_of = [](int cnt) { return cnt <= 1 ? 1 : 1 << (32 - __clz(cnt - 1)); };
-  // after a window lands: a short (last) window is padded with +inf up to its
-  // search depth, so that the fixed-depth search needs no bounds test
+  // after a window lands: the last window is padded with +inf up to and including
+  // its search depth, so that the fixed-depth search needs no bounds test and the
+  // slot after any search result reads +inf (every other window is full, and a
+  // key searched in it is at most its last element)
   auto land = [&](int wj) {
+    if (lane == 0) N2V_STAT(kStatWindows, 1);
     stage_wait(sm, wj & (sm.nbuf - 1));
-    const int cnt = min(W, llen - wj * W);
-    const int depth = depth_of(cnt);
-    if (cnt < depth) {
+    if (wj == nwin - 1) {
+      const int cnt = llen - wj * W;
+      const int depth = depth_of(cnt);
       int32_t* w = sm.win + (wj & (sm.nbuf - 1)) * (sm.wlen + 8) + stage_off(sm, L, wj);
-      for (int q = cnt + lane; q < depth; q += 32) w[q] = INT32_MAX;
+      for (int q = cnt + lane; q <= depth; q += 32) w[q] = INT32_MAX;
       __syncwarp();
     }
   };
@@ -464,6 +467,7 @@ __device__ __forceinline__ void gen_specials(StepCtx& c, int mode, int32_t hub, 
   land(0);
   set_window(0);
   for (int kc = c.cb; kc < nkeys; kc += 64) {
+    if (lane == 0) N2V_STAT(kStatChunks, 1);
     const int i0 = kc + lane, i1 = kc + 32 + lane;
     const int32_t key0 = next0, key1 = next1;
     next0 = after0;
@@ -478,15 +482,18 @@ __device__ __forceinline__ void gen_specials(StepCtx& c, int mode, int32_t hub, 
     for (;;) {
       const bool go0 = pend0 && (wlast_inf || key0 <= wlast);
       const bool go1 = pend1 && (wlast_inf || key1 <= wlast);
+      if (lane == 0) N2V_STAT(kStatSearches, 1);
       if (go0 || go1) {
         // fixed-depth searches over the power-of-two window (slots [wcnt, wdepth) hold +inf)
         int lo0, lo1;
         window_rank2_any(wdepth, wbase, key0, key1, lo0, lo1);
-        N2V_CHECK(g, lo0 >= 0 && lo0 <= wcnt && lo1 >= 0 && lo1 <= wcnt && wcnt <= W);
-        if (lo0 < wcnt && lds32(wbase + 4u * lo0) < key0) ++lo0;
-        if (lo1 < wcnt && lds32(wbase + 4u * lo1) < key1) ++lo1;
-        if (go0 && lo0 < wcnt && lds32(wbase + 4u * lo0) == key0) at0 = c.lb + wi * W + lo0;
-        if (go1 && lo1 < wcnt && lds32(wbase + 4u * lo1) == key1) at1 = c.lb + wi * W + lo1;
+        N2V_CHECK(g, lo0 >= 0 && lo0 < wdepth && lo1 >= 0 && lo1 < wdepth && wcnt <= W);
+        // the lower bound is lo or lo + 1: both slots in one round trip (slot lo + 1 holds
+        // data, or +inf past the end of the last window)
+        const int32_t x0 = lds32(wbase + 4u * lo0), y0 = lds32(wbase + 4u * (lo0 + 1));
+        const int32_t x1 = lds32(wbase + 4u * lo1), y1 = lds32(wbase + 4u * (lo1 + 1));
+        if (go0 && (x0 == key0 || (x0 < key0 && y0 == key0))) at0 = c.lb + wi * W + lo0 + (x0 == key0 ? 0 : 1);
+        if (go1 && (x1 == key1 || (x1 < key1 && y1 == key1))) at1 = c.lb + wi * W + lo1 + (x1 == key1 ? 0 : 1);
         pend0 = pend0 && !go0;
         pend1 = pend1 && !go1;
       }
@@ -882,13 +889,25 @@ __device__ __forceinline__ int32_t warp_step(const GraphView& g, int64_t t, int6
   if (pl.mode == 1) find_t_slot(c);  // walks S in order (mode 2 finds t's slot while its copies fly)
   // pass 1: every special (their corrections give T), the first `keep` of them kept
   SpecialSink sk = new_sink(sm, c.dv);
+#ifdef N2V_STATS
+  const long long t_gen = clock64();
+#endif
   gen_specials(c, pl.mode, pl.hub, pl.bm, sm, sk, a_p, a_q, lane);
   const uint64_t Wv = static_prefix(g, bv, c.dv - 1);
   const uint64_t T = (uint64_t)a_q * Wv + sink_correction(g, sk, a_p, a_q);
   if (T == 0) return -1;
   if (lane == 0 && sk.cnt > sk.cap) N2V_STAT(kStatSpilled, 1);
+#ifdef N2V_STATS
+  const long long t_sel = clock64();
+#endif
   const int chosen = select_range(c, pl, sm, sk, scale_draw(u, T), 0ull, -1, c.dv - 1, a_p, a_q, lane);
   __syncwarp();
+#ifdef N2V_STATS
+  if (lane == 0 && (pl.mode == 2 || pl.mode == 3)) {
+    N2V_STAT(kStatGenCycles, t_sel - t_gen);
+    N2V_STAT(kStatSelCycles, clock64() - t_sel);
+  }
+#endif
 #ifdef N2V_STATS
   stat();
 #endif
