@@ -179,12 +179,6 @@ __device__ __forceinline__ int lower_bound32(const int32_t* __restrict__ a, int 
   return lo;
 }
 
-// Keys a lane searches per chunk in the staged generator (interleaved chains).
-#ifndef N2V_STAGE_KEYS
-#define N2V_STAGE_KEYS 4
-#endif
-constexpr int kStageKeys = N2V_STAGE_KEYS;
-
 // Element offset of L[wi * wlen] inside its staging buffer (the copy starts at
 // the 16-byte boundary below it).
 __device__ __forceinline__ int stage_off(const WarpSmem& sm, const int32_t* L, int wi) {
@@ -213,47 +207,6 @@ __device__ __forceinline__ void window_rank2(uint32_t base, int32_t key0, int32_
   }
   lo0 = a;
   lo1 = b;
-}
-
-// NK interleaved fixed-depth searches: lo[q] = slots below key[q] among the
-// first W - 1 (the lower bound is lo[q] or lo[q] + 1).
-template <int W, int NK>
-__device__ __forceinline__ void window_rankN(uint32_t base, const int32_t (&key)[NK], int (&lo)[NK]) {
-  int a[NK];
-#pragma unroll
-  for (int q = 0; q < NK; ++q) a[q] = 0;
-#pragma unroll
-  for (int st = W >> 1; st > 0; st >>= 1) {
-    int32_t v[NK];
-#pragma unroll
-    for (int q = 0; q < NK; ++q) v[q] = lds32(base + 4u * (uint32_t)(a[q] + st - 1));
-#pragma unroll
-    for (int q = 0; q < NK; ++q) a[q] += v[q] < key[q] ? st : 0;
-  }
-#pragma unroll
-  for (int q = 0; q < NK; ++q) lo[q] = a[q];
-}
-
-// The same over a window of depth slots (a power of two): unrolled for full
-// 1024-element windows, a loop for every other depth.
-template <int NK>
-__device__ __forceinline__ void window_rank_any(int depth, uint32_t base, const int32_t (&key)[NK], int (&lo)[NK]) {
-  if (depth == 1024) {
-    window_rankN<1024, NK>(base, key, lo);
-    return;
-  }
-  int a[NK];
-#pragma unroll
-  for (int q = 0; q < NK; ++q) a[q] = 0;
-  for (int st = depth >> 1; st > 0; st >>= 1) {
-    int32_t v[NK];
-#pragma unroll
-    for (int q = 0; q < NK; ++q) v[q] = lds32(base + 4u * (uint32_t)(a[q] + st - 1));
-#pragma unroll
-    for (int q = 0; q < NK; ++q) a[q] += v[q] < key[q] ? st : 0;
-  }
-#pragma unroll
-  for (int q = 0; q < NK; ++q) lo[q] = a[q];
 }
 
 // The same search over a window of depth slots (a power of two): unrolled for
@@ -509,77 +462,71 @@ __device__ __forceinline__ void gen_specials(StepCtx& c, int mode, int32_t hub, 
     wlast_inf = wj == nwin - 1;
     wlast = lds32(wbase + 4u * (uint32_t)(wcnt - 1));
   };
-  // kStageKeys keys per lane and chunk (keys kc + 32 q + lane): that many independent
-  // search chains in flight per lane; the next chunk's keys load while one is searched
-  constexpr int NK = kStageKeys;
-  int32_t nxt[NK];
-#pragma unroll
-  for (int q = 0; q < NK; ++q) nxt[q] = key_at(c.cb + 32 * q + lane);
+  int32_t next0 = key_at(c.cb + lane), next1 = key_at(c.cb + 32 + lane);
+  int32_t after0 = key_at(c.cb + 64 + lane), after1 = key_at(c.cb + 96 + lane);
   land(0);
   set_window(0);
-  for (int kc = c.cb; kc < nkeys; kc += 32 * NK) {
+  for (int kc = c.cb; kc < nkeys; kc += 64) {
     if (lane == 0) N2V_STAT(kStatChunks, 1);
-    int32_t key[NK];
-    bool is_t[NK], pend[NK];
-    int at[NK];  // index of the key inside N(v) (stage N(v)) or found in N(t) (stage N(t)), or -1
-#pragma unroll
-    for (int q = 0; q < NK; ++q) {
-      const int i = kc + 32 * q + lane;
-      key[q] = nxt[q];
-      nxt[q] = key_at(i + 32 * NK);
-      // an element of N(v) equal to t is special whatever N(t) holds
-      is_t[q] = i < nkeys && !stage_v && key[q] == c.t32;
-      pend[q] = i < nkeys && !is_t[q];
-      at[q] = -1;
-    }
+    const int i0 = kc + lane, i1 = kc + 32 + lane;
+    const int32_t key0 = next0, key1 = next1;
+    next0 = after0;
+    next1 = after1;
+    after0 = key_at(i0 + 128);
+    after1 = key_at(i1 + 128);
+    // an element of N(v) equal to t is special whatever N(t) holds
+    const bool is_t0 = i0 < nkeys && !stage_v && key0 == c.t32;
+    const bool is_t1 = i1 < nkeys && !stage_v && key1 == c.t32;
+    bool pend0 = i0 < nkeys && !is_t0, pend1 = i1 < nkeys && !is_t1;
+    int at0 = -1, at1 = -1;  // index of the key inside L, or -1
     for (;;) {
-      bool go[NK], any_go = false, any_pend = false;
-#pragma unroll
-      for (int q = 0; q < NK; ++q) {
-        go[q] = pend[q] && (wlast_inf || key[q] <= wlast);
-        any_go |= go[q];
-      }
+      const bool go0 = pend0 && (wlast_inf || key0 <= wlast);
+      const bool go1 = pend1 && (wlast_inf || key1 <= wlast);
       if (lane == 0) N2V_STAT(kStatSearches, 1);
-      if (any_go) {
-        // fixed-depth searches over the power-of-two window (slots [wcnt, wdepth] hold +inf)
-        int lo[NK];
-        window_rank_any<NK>(wdepth, wbase, key, lo);
-#pragma unroll
-        for (int q = 0; q < NK; ++q) {
-          N2V_CHECK(g, lo[q] >= 0 && lo[q] < wdepth && wcnt <= W);
-          // the lower bound is lo or lo + 1: both slots in one round trip (slot lo + 1 holds
-          // data, or +inf past the end of the last window)
-          const int32_t x = lds32(wbase + 4u * lo[q]), y = lds32(wbase + 4u * (lo[q] + 1));
-          if (go[q] && (x == key[q] || (x < key[q] && y == key[q])))
-            at[q] = c.lb + wi * W + lo[q] + (x == key[q] ? 0 : 1);
-          pend[q] = pend[q] && !go[q];
-        }
+      if (go0 || go1) {
+        // fixed-depth searches over the power-of-two window (slots [wcnt, wdepth) hold +inf)
+        int lo0, lo1;
+        window_rank2_any(wdepth, wbase, key0, key1, lo0, lo1);
+        N2V_CHECK(g, lo0 >= 0 && lo0 < wdepth && lo1 >= 0 && lo1 < wdepth && wcnt <= W);
+        // the lower bound is lo or lo + 1: both slots in one round trip (slot lo + 1 holds
+        // data, or +inf past the end of the last window)
+        const int32_t x0 = lds32(wbase + 4u * lo0), y0 = lds32(wbase + 4u * (lo0 + 1));
+        const int32_t x1 = lds32(wbase + 4u * lo1), y1 = lds32(wbase + 4u * (lo1 + 1));
+        if (go0 && (x0 == key0 || (x0 < key0 && y0 == key0))) at0 = c.lb + wi * W + lo0 + (x0 == key0 ? 0 : 1);
+        if (go1 && (x1 == key1 || (x1 < key1 && y1 == key1))) at1 = c.lb + wi * W + lo1 + (x1 == key1 ? 0 : 1);
+        pend0 = pend0 && !go0;
+        pend1 = pend1 && !go1;
       }
-#pragma unroll
-      for (int q = 0; q < NK; ++q) any_pend |= pend[q];
-      if (!__any_sync(kFull, any_pend)) break;
+      if (!__any_sync(kFull, pend0 || pend1)) break;
       __syncwarp();
       if (wi + sm.nbuf < nwin) stage_issue(sm, g, L, llen, wi + sm.nbuf, lane);
       ++wi;
       land(wi);
       set_window(wi);
     }
-#pragma unroll
-    for (int q = 0; q < NK; ++q) {
-      const int i = kc + 32 * q + lane;
-      int32_t pos = -1;
-      uint32_t cls = 0;
-      if (stage_v) {
-        if (at[q] >= 0) {
-          pos = at[q];
-          cls = key[q] == c.t32 ? 2u : 1u;
-        }
-      } else if (is_t[q] || at[q] >= 0) {
-        pos = i;
-        cls = is_t[q] ? 2u : 1u;
+    int32_t pos0 = -1, pos1 = -1;
+    uint32_t cls0 = 0, cls1 = 0;
+    if (stage_v) {
+      if (at0 >= 0) {
+        pos0 = at0;
+        cls0 = key0 == c.t32 ? 2u : 1u;
       }
-      if (kc + 32 * q < nkeys) sink_emit(k, sm, g, c.bv, pos, cls, a_p, a_q, lane);
+      if (at1 >= 0) {
+        pos1 = at1;
+        cls1 = key1 == c.t32 ? 2u : 1u;
+      }
+    } else {
+      if (is_t0 || at0 >= 0) {
+        pos0 = i0;
+        cls0 = is_t0 ? 2u : 1u;
+      }
+      if (is_t1 || at1 >= 0) {
+        pos1 = i1;
+        cls1 = is_t1 ? 2u : 1u;
+      }
     }
+    sink_emit(k, sm, g, c.bv, pos0, cls0, a_p, a_q, lane);
+    if (kc + 32 < nkeys) sink_emit(k, sm, g, c.bv, pos1, cls1, a_p, a_q, lane);
   }
   // the windows after the current one may still be in flight
   for (int q = wi + 1; q < nwin && q <= wi + sm.nbuf - 1; ++q) stage_wait(sm, q & (sm.nbuf - 1));
