@@ -310,6 +310,43 @@ __device__ __forceinline__ void sink_emit(SpecialSink& k, WarpSmem& sm, const Gr
   k.cnt += __popc(m);
 }
 
+// Keep special `pos` (class cls) at ordinal ord of the step (before the skip).
+__device__ __forceinline__ void sink_store(SpecialSink& k, WarpSmem& sm, const GraphView& g, int32_t pos,
+                                           uint32_t cls, int ord) {
+  ord -= k.skip;
+  N2V_CHECK(g, pos >= 0 && pos < k.lim);
+  if (ord >= 0 && ord < k.keep) {
+    const uint32_t e = (uint32_t)pos | (cls << 30);
+    if (ord < k.cap) {
+      sm.spec[ord] = e;
+    } else {
+      N2V_CHECK(g, sm.spill != nullptr && ord - k.cap < sm.spill_cap);
+      sm.spill[ord - k.cap] = e;
+    }
+  }
+}
+
+// sink_emit for the two candidate sets of a chunk at once (set 1 follows set 0
+// in position order; has1: set 1 exists, uniform).  The x == t special can be
+// in the chunk only when maybe_t (uniform); then one vote finds it.
+__device__ __forceinline__ void sink_emit2(SpecialSink& k, WarpSmem& sm, const GraphView& g, int64_t bv, int32_t pos0,
+                                           uint32_t cls0, int32_t pos1, uint32_t cls1, bool has1, bool maybe_t,
+                                           uint32_t a_p, uint32_t a_q, int lane) {
+  if (g.w) k.dpart += special_delta(g, bv, pos0, cls0, a_p, a_q) + special_delta(g, bv, pos1, cls1, a_p, a_q);
+  const unsigned m0 = __ballot_sync(kFull, cls0 != 0u);
+  const unsigned m1 = has1 ? __ballot_sync(kFull, cls1 != 0u) : 0u;
+  const int n0 = __popc(m0);
+  if (maybe_t) {
+    const unsigned t0 = __ballot_sync(kFull, cls0 == 2u), t1 = __ballot_sync(kFull, cls1 == 2u);
+    if (t0) k.ord_t = k.cnt + __popc(m0 & ((1u << (__ffs(t0) - 1)) - 1u));
+    else if (t1) k.ord_t = k.cnt + n0 + __popc(m1 & ((1u << (__ffs(t1) - 1)) - 1u));
+  }
+  const unsigned lt = lanemask_lt();
+  if (cls0) sink_store(k, sm, g, pos0, cls0, k.cnt + __popc(m0 & lt));
+  if (cls1) sink_store(k, sm, g, pos1, cls1, k.cnt + n0 + __popc(m1 & lt));
+  k.cnt += n0 + __popc(m1);
+}
+
 // Enumerate the specials of the step in increasing position into `k`.
 // mode 0: probe over N(v) (membership in N(t)); 1: probe over S (position in
 // N(v)); 2: stage N(v), candidates S; 3: stage N(t), candidates N(v).
@@ -431,7 +468,15 @@ __device__ __forceinline__ void gen_specials(StepCtx& c, int mode, int32_t hub, 
   int wi = 0;
   // two keys per lane and chunk (keys kc + lane and kc + 32 + lane): two
   // independent search chains in flight per lane
-  auto key_at = [&](int i) -> int32_t { return i < nkeys ? (stage_v ? s_at(c, i) : __ldg(c.nv + i)) : 0; };
+  // key i (clamped into the list: keys past the end are never searched), without branches:
+  // element i of S = N(t) + {t} is t at t's slot, else N(t)[i] or N(t)[i - 1]
+  const int ins_e = c.has_self ? INT32_MAX : c.ins;
+  auto key_at = [&](int i) -> int32_t {
+    const int j = min(i, nkeys - 1);
+    if (!stage_v) return __ldg(c.nv + j);
+    const int32_t x = __ldg(c.nt + min(j - (j > ins_e ? 1 : 0), c.dt - 1));
+    return j == ins_e ? c.t32 : x;
+  };
   // search depth of a window holding cnt elements: the next power of two
   auto depth_of = [](int cnt) { return cnt <= 1 ? 1 : 1 << (32 - __clz(cnt - 1)); };
   // after a window lands: the last window is padded with +inf up to and including
@@ -504,29 +549,16 @@ __device__ __forceinline__ void gen_specials(StepCtx& c, int mode, int32_t hub, 
       land(wi);
       set_window(wi);
     }
-    int32_t pos0 = -1, pos1 = -1;
-    uint32_t cls0 = 0, cls1 = 0;
-    if (stage_v) {
-      if (at0 >= 0) {
-        pos0 = at0;
-        cls0 = key0 == c.t32 ? 2u : 1u;
-      }
-      if (at1 >= 0) {
-        pos1 = at1;
-        cls1 = key1 == c.t32 ? 2u : 1u;
-      }
-    } else {
-      if (is_t0 || at0 >= 0) {
-        pos0 = i0;
-        cls0 = is_t0 ? 2u : 1u;
-      }
-      if (is_t1 || at1 >= 0) {
-        pos1 = i1;
-        cls1 = is_t1 ? 2u : 1u;
-      }
-    }
-    sink_emit(k, sm, g, c.bv, pos0, cls0, a_p, a_q, lane);
-    if (kc + 32 < nkeys) sink_emit(k, sm, g, c.bv, pos1, cls1, a_p, a_q, lane);
+    // stage N(v): the key's index in N(v), class 2 for the key t; stage N(t): the key's own
+    // index, class 2 for the key t (special whatever N(t) holds)
+    const bool f0 = stage_v ? at0 >= 0 : (is_t0 || at0 >= 0);
+    const bool f1 = stage_v ? at1 >= 0 : (is_t1 || at1 >= 0);
+    const int32_t pos0 = f0 ? (stage_v ? at0 : i0) : -1, pos1 = f1 ? (stage_v ? at1 : i1) : -1;
+    const uint32_t cls0 = f0 ? (key0 == c.t32 ? 2u : 1u) : 0u, cls1 = f1 ? (key1 == c.t32 ? 2u : 1u) : 0u;
+    // the key t lies in this chunk: stage N(v) knows its slot in S; stage N(t) asks the lanes
+    // (t's index in S is c.ins, also when t is in N(t) through a self-loop)
+    const bool maybe_t = stage_v ? (c.ins >= kc && c.ins < kc + 64) : __any_sync(kFull, is_t0 || is_t1);
+    sink_emit2(k, sm, g, c.bv, pos0, cls0, pos1, cls1, kc + 32 < nkeys, maybe_t, a_p, a_q, lane);
   }
   // the windows after the current one may still be in flight
   for (int q = wi + 1; q < nwin && q <= wi + sm.nbuf - 1; ++q) stage_wait(sm, q & (sm.nbuf - 1));
