@@ -192,21 +192,34 @@ __device__ __forceinline__ int32_t lds32(uint32_t addr) {
   return v;
 }
 
-// Number of window slots below key0 and key1 in a sorted window of W slots
-// (W a power of two; slots past the data hold +inf) at shared address base:
-// two interleaved fixed-depth searches, fully unrolled.
+// One level of two interleaved fixed-depth searches: the positions are kept as
+// shared addresses, and the level's probe offset 4 (ST - 1) is an immediate of
+// the load, so that a level is one load, one compare and one add per key.
+template <int ST>
+struct WindowLevels {
+  __device__ __forceinline__ static void run(uint32_t& p0, uint32_t& p1, int32_t key0, int32_t key1) {
+    int32_t v0, v1;
+    asm volatile("ld.shared.s32 %0, [%1+%2];" : "=r"(v0) : "r"(p0), "n"(4 * (ST - 1)));
+    asm volatile("ld.shared.s32 %0, [%1+%2];" : "=r"(v1) : "r"(p1), "n"(4 * (ST - 1)));
+    p0 += v0 < key0 ? 4u * ST : 0u;
+    p1 += v1 < key1 ? 4u * ST : 0u;
+    WindowLevels<ST / 2>::run(p0, p1, key0, key1);
+  }
+};
+template <>
+struct WindowLevels<0> {
+  __device__ __forceinline__ static void run(uint32_t&, uint32_t&, int32_t, int32_t) {}
+};
+
+// Number of window slots below key0 and key1 among the first W - 1 of a sorted
+// window of W slots (W a power of two; slots past the data hold +inf) at shared
+// address base: two interleaved fixed-depth searches, fully unrolled.
 template <int W>
 __device__ __forceinline__ void window_rank2(uint32_t base, int32_t key0, int32_t key1, int& lo0, int& lo1) {
-  int a = 0, b = 0;
-#pragma unroll
-  for (int st = W >> 1; st > 0; st >>= 1) {
-    const int32_t v0 = lds32(base + 4u * (uint32_t)(a + st - 1));
-    const int32_t v1 = lds32(base + 4u * (uint32_t)(b + st - 1));
-    a += v0 < key0 ? st : 0;
-    b += v1 < key1 ? st : 0;
-  }
-  lo0 = a;
-  lo1 = b;
+  uint32_t p0 = base, p1 = base;
+  WindowLevels<W / 2>::run(p0, p1, key0, key1);
+  lo0 = (int)((p0 - base) >> 2);
+  lo1 = (int)((p1 - base) >> 2);
 }
 
 // The same search over a window of depth slots (a power of two): unrolled for
