@@ -400,9 +400,8 @@ int n2v_stored_walk(const n2v_graph* g, const void* table, const int32_t* starts
  * of their shorter and longer lists (layout: lane-tier batches and cycles,
  * first steps and cycles, then four words per generator mode 0..4, then
  * segment re-enumerations, spilled steps, the warps' total cycles in the
- * persistent loop, and for the staged steps the cycles of their first
- * enumeration and of their selection, their chunks of keys, windows landed
- * and window searches).  Synchronises the device; reset != 0 zeroes the counters.
+ * persistent loop, and for the staged steps their chunks of keys, windows
+ * landed and window searches).  Synchronises the device; reset != 0 zeroes the counters.
  * Other builds fill out with zeros and return N2V_ERR_INVALID_ARG.  n <= 32. */
 int n2v_step_stats(uint64_t* out, int32_t n, int32_t reset);
 

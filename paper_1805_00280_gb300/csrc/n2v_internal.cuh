@@ -45,11 +45,9 @@ enum : int {
   kStatSegments = 24,    // re-enumerations of a step's specials (segments beyond the first)
   kStatSpilled = 25,     // steps whose specials overflowed shared memory
   kStatKernelCycles = 26,  // sum over warps of their time in the persistent loop
-  kStatGenCycles = 27,     // staged steps: cycles of the first enumeration of the specials
-  kStatSelCycles = 28,     // staged steps: cycles of the selection (including re-enumerations)
-  kStatChunks = 29,        // staged steps: chunks of 64 keys
-  kStatWindows = 30,       // staged steps: windows landed
-  kStatSearches = 31,      // staged steps: window searches (a chunk's keys in one window)
+  kStatChunks = 27,        // staged steps: chunks of 64 keys
+  kStatWindows = 28,       // staged steps: windows landed
+  kStatSearches = 29,      // staged steps: window searches (a chunk's keys in one window)
   kStatWords = 32
 };
 #ifdef N2V_STATS
@@ -169,6 +167,12 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     if (clock64() - t0 > limit) return false;
   }
   return true;
+}
+
+// Drop the 128-byte L2 line at p (128-byte aligned) without writing it back:
+// its data becomes undefined.  For scratch that is dead once read.
+__device__ __forceinline__ void discard_l2_line(const void* p) {
+  asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
 }
 
 // ---------------------------------------------------------------------------

@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(kPersistThreads, 5)
     const int64_t i = (int64_t)base - S.slot_begin + lane;
     const bool mine = i < S.count;
     const int64_t wid = S.walk_begin + i;
-    RowOut out = row_out(S.walks + wid * (int64_t)S.l);
+    int32_t* row = S.walks + wid * (int64_t)S.l;
     int64_t t = -1, v = -1;
     bool alive = false;
     if (mine) {
@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(kPersistThreads, 5)
       J.a_q = S.a_q;
       J.approx = 0;
       const int32_t x = warp_binned_step(g, alive, t, v, k, (uint64_t)wid, J, L.thread_max_deg, sm, L.stream_ratio, lane);
-      if (mine) row_put(out, k, alive ? x : -1);
+      if (mine) row[k] = alive ? x : -1;
       if (alive) {
         if (x < 0) {
           alive = false;
@@ -91,7 +91,8 @@ __global__ void __launch_bounds__(kPersistThreads, 5)
         }
       }
     }
-    if (mine) row_finish(out, k, S.l);  // the last group, and -1 after the walk ended
+    if (mine)
+      for (int kk = k; kk < S.l; ++kk) row[kk] = -1;  // after the walk ended
   }
   if (sm.timed_out && lane == 0) atomicOr(status, kStTimeout);
 }

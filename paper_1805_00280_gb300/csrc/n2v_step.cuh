@@ -743,14 +743,17 @@ __device__ __forceinline__ uint64_t sink_correction(const GraphView& g, const Sp
 }
 
 // The chosen position, given that it lies in the position range (prev0, hi]
-// of N(v), that C_j = a_q W_j + D_j with D = D0 just before the range, and
-// that `sk` holds the first enumeration of the range's specials (those with
-// ordinals [0, keep) kept).  Pass 2 walks the kept specials in position order;
-// if the answer lies beyond them, the range is enumerated again keeping the
-// next segment, and the walk continues from where it stopped.
+// of N(v) and that C_j = a_q W_j + D_j with D = D0 just before the range.
+// Pass 1 enumerates the range's specials, keeping ordinals [0, keep): done by
+// the caller when first_done (with r given), else here, where its corrections
+// give T = Tbase + their sum and r = floor(u T / 2^64) (-2 is returned when
+// T == 0: a dead end).  Pass 2 walks the kept specials in position order; if
+// the answer lies beyond them, the range is enumerated again keeping the next
+// segment, and the walk continues from where it stopped.  The generator has
+// one call site here, so the step's largest code is inlined once.
 __device__ __forceinline__ int select_range(StepCtx& c, const StepPlan& pl, WarpSmem& sm, SpecialSink& sk,
-                                            uint64_t r, uint64_t D0, int prev0, int hi_pos, uint32_t a_p,
-                                            uint32_t a_q, int lane) {
+                                            bool first_done, uint64_t& r, uint64_t u, uint64_t Tbase, uint64_t D0,
+                                            int prev0, int hi_pos, uint32_t a_p, uint32_t a_q, int lane) {
   const GraphView& g = *c.g;
   const int64_t bv = c.bv;
   uint64_t D = D0;
@@ -758,12 +761,18 @@ __device__ __forceinline__ int select_range(StepCtx& c, const StepPlan& pl, Warp
   bool found = false;
   const uint64_t d1 = (uint64_t)kAlphaOne - (uint64_t)a_q, d2 = (uint64_t)a_p - (uint64_t)a_q;
   for (int seg = 0;; seg += sk.keep) {
-    if (seg > 0) {
-      if (lane == 0) N2V_STAT(kStatSegments, 1);
+    if (seg > 0 || !first_done) {
+      if (seg > 0 && lane == 0) N2V_STAT(kStatSegments, 1);
       sk.cnt = 0;
       sk.ord_t = -1;
       sk.skip = seg;
       gen_specials(c, pl.mode, pl.hub, pl.bm, sm, sk, a_p, a_q, lane);
+      if (seg == 0) {
+        const uint64_t T = Tbase + sink_correction(g, sk, a_p, a_q);
+        if (T == 0) return -2;
+        r = scale_draw(u, T);
+        if (lane == 0 && sk.cnt > sk.cap) N2V_STAT(kStatSpilled, 1);
+      }
     }
     __syncwarp();
     __threadfence_block();  // spilled specials are read back by other lanes
@@ -872,6 +881,15 @@ __device__ __forceinline__ int select_range(StepCtx& c, const StepPlan& pl, Warp
     }
   }
   N2V_CHECK(g, chosen > prev0 && chosen <= hi_pos && chosen < c.dv);
+  // the spilled specials are dead: drop their L2 lines instead of letting them be written back
+  // (only lines wholly inside this warp's used part of its spill area)
+  if (sm.spill && sk.cnt > sk.cap) {
+    const uintptr_t b0 = (uintptr_t)sm.spill;
+    const uintptr_t e0 = b0 + 4u * (uintptr_t)(min(sk.cnt, sk.keep) - sk.cap);
+    const uintptr_t first = (b0 + 127u) & ~(uintptr_t)127u, last = e0 & ~(uintptr_t)127u;
+    __syncwarp();
+    for (uintptr_t a = first + 128u * (uintptr_t)lane; a < last; a += 128u * 32u) discard_l2_line((const void*)a);
+  }
   return chosen;
 }
 
@@ -932,27 +950,13 @@ __device__ __forceinline__ int32_t warp_step(const GraphView& g, int64_t t, int6
     return x;
   }
   if (pl.mode == 1) find_t_slot(c);  // walks S in order (mode 2 finds t's slot while its copies fly)
-  // pass 1: every special (their corrections give T), the first `keep` of them kept
+  // every special (their corrections give T), then the selection
   SpecialSink sk = new_sink(sm, c.dv);
-#ifdef N2V_STATS
-  const long long t_gen = clock64();
-#endif
-  gen_specials(c, pl.mode, pl.hub, pl.bm, sm, sk, a_p, a_q, lane);
-  const uint64_t Wv = static_prefix(g, bv, c.dv - 1);
-  const uint64_t T = (uint64_t)a_q * Wv + sink_correction(g, sk, a_p, a_q);
-  if (T == 0) return -1;
-  if (lane == 0 && sk.cnt > sk.cap) N2V_STAT(kStatSpilled, 1);
-#ifdef N2V_STATS
-  const long long t_sel = clock64();
-#endif
-  const int chosen = select_range(c, pl, sm, sk, scale_draw(u, T), 0ull, -1, c.dv - 1, a_p, a_q, lane);
+  uint64_t r = 0;
+  const int chosen = select_range(c, pl, sm, sk, false, r, u, (uint64_t)a_q * static_prefix(g, bv, c.dv - 1), 0ull,
+                                  -1, c.dv - 1, a_p, a_q, lane);
+  if (chosen < 0) return -1;  // T == 0
   __syncwarp();
-#ifdef N2V_STATS
-  if (lane == 0 && (pl.mode == 2 || pl.mode == 3)) {
-    N2V_STAT(kStatGenCycles, t_sel - t_gen);
-    N2V_STAT(kStatSelCycles, clock64() - t_sel);
-  }
-#endif
 #ifdef N2V_STATS
   stat();
 #endif
@@ -1050,7 +1054,8 @@ __device__ __forceinline__ int32_t block_step(const GraphView& g, int64_t t, int
     }
 #endif
     if (P_lo < P_hi && C_before <= r && r < C_end) {
-      const int j = select_range(c, pl, sm, sk, r, Dw, P_lo - 1, P_hi - 1, a_p, a_q, lane);
+      uint64_t rr = r;
+      const int j = select_range(c, pl, sm, sk, true, rr, 0ull, 0ull, Dw, P_lo - 1, P_hi - 1, a_p, a_q, lane);
       if (lane == 0) bs->result = __ldg(c.nv + j);
     }
   }
@@ -1086,56 +1091,6 @@ __device__ __forceinline__ int32_t static_step(const GraphView& g, int64_t bv, i
 __device__ __forceinline__ bool approx_here(const WalkJob& J, int k, int64_t dv, int64_t dt) {
   return J.approx && k > 0 && dv >= J.approx_popular && dt < J.approx_popular &&
          approx_decide(dv, dt, J.a_p, J.a_q, J.w_min, J.w_max, J.approx_eps);
-}
-
-// ---------------------------------------------------------------------------
-// Output of one walker's row: the vertices of steps 4m .. 4m+3 are kept in
-// registers and written by one 16-byte store where the row is 16-byte aligned
-// (one sector touched per four steps instead of one per step), else one by one.
-struct RowOut {
-  int32_t* row;
-  int32_t o0, o1, o2;
-  bool vec;
-};
-
-__device__ __forceinline__ RowOut row_out(int32_t* row) {
-  RowOut b;
-  b.row = row;
-  b.o0 = b.o1 = b.o2 = -1;
-  b.vec = ((uintptr_t)row & 15) == 0;
-  return b;
-}
-
-// Record step k's vertex y (k is the same in every lane of the warp).
-__device__ __forceinline__ void row_put(RowOut& b, int k, int32_t y) {
-  switch (k & 3) {
-    case 0: b.o0 = y; break;
-    case 1: b.o1 = y; break;
-    case 2: b.o2 = y; break;
-    default:
-      if (b.vec) {
-        *reinterpret_cast<int4*>(b.row + (k - 3)) = make_int4(b.o0, b.o1, b.o2, y);
-      } else {
-        b.row[k - 3] = b.o0;
-        b.row[k - 2] = b.o1;
-        b.row[k - 1] = b.o2;
-        b.row[k] = y;
-      }
-  }
-}
-
-// Write the steps of the current group below k, then -1 at steps k .. l-1.
-__device__ __forceinline__ void row_finish(const RowOut& b, int k, int l) {
-  const int k0 = k & ~3, s = k & 3;
-  if (s > 0) b.row[k0] = b.o0;
-  if (s > 1) b.row[k0 + 1] = b.o1;
-  if (s > 2) b.row[k0 + 2] = b.o2;
-  int kk = k;
-  if (b.vec) {
-    for (; kk < l && (kk & 3); ++kk) b.row[kk] = -1;
-    for (; kk + 4 <= l; kk += 4) *reinterpret_cast<int4*>(b.row + kk) = make_int4(-1, -1, -1, -1);
-  }
-  for (; kk < l; ++kk) b.row[kk] = -1;
 }
 
 // ---------------------------------------------------------------------------

@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(kPersistThreads, MINB)
     const int64_t i = (int64_t)base + lane;
     const bool mine = i < J.count;
     const int64_t wid = J.walk_begin + i;
-    RowOut out = row_out(J.walks + i * (int64_t)J.l);
+    int32_t* row = J.walks + i * (int64_t)J.l;
     int64_t t = -1, v = -1;
     bool alive = false;
     if (mine) {
@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(kPersistThreads, MINB)
       const int32_t x = warp_binned_step(g, alive, t, v, k, (uint64_t)wid, J, L.thread_max_deg, sm, L.stream_ratio,
                                          lane);
       N2V_CHECK(g, !alive || (x >= -1 && x < g.n));
-      if (mine) row_put(out, k, alive ? x : -1);
+      if (mine) row[k] = alive ? x : -1;
       if (alive) {
         if (x < 0) {
           alive = false;
@@ -140,7 +140,8 @@ __global__ void __launch_bounds__(kPersistThreads, MINB)
         }
       }
     }
-    if (mine) row_finish(out, k, J.l);  // the last group, and -1 after the walk ended
+    if (mine)
+      for (int kk = k; kk < J.l; ++kk) row[kk] = -1;
   }
 #ifdef N2V_STATS
   if (lane == 0) N2V_STAT(kStatKernelCycles, clock64() - t_kernel);
@@ -176,7 +177,7 @@ __global__ void __launch_bounds__(kPersistThreads, MINB)
     const int64_t i = base + tid;
     const bool mine = i < J.count;
     const int64_t wid = J.walk_begin + i;
-    RowOut out = row_out(J.walks + i * (int64_t)J.l);
+    int32_t* row = J.walks + i * (int64_t)J.l;
     int64_t t = -1, v = -1;
     bool alive = false;
     if (mine) {
@@ -194,7 +195,7 @@ __global__ void __launch_bounds__(kPersistThreads, MINB)
       if (!__syncthreads_or(alive)) break;
       const int32_t x = block_binned_step(g, alive, t, v, k, (uint64_t)wid, J, L, sm, bq, warp, lane, tid);
       N2V_CHECK(g, !alive || (x >= -1 && x < g.n));
-      if (mine) row_put(out, k, alive ? x : -1);
+      if (mine) row[k] = alive ? x : -1;
       if (alive) {
         if (x < 0) {
           alive = false;
@@ -204,7 +205,8 @@ __global__ void __launch_bounds__(kPersistThreads, MINB)
         }
       }
     }
-    if (mine) row_finish(out, k, J.l);
+    if (mine)
+      for (int kk = k; kk < J.l; ++kk) row[kk] = -1;
     if (__syncthreads_or(sm.timed_out)) break;  // also: nobody reads bq before thread 0 rewrites it
   }
   if (sm.timed_out && lane == 0) atomicOr(J.status, kStTimeout);

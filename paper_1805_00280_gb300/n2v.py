@@ -287,8 +287,8 @@ def n2v_launch_shape(handle: int) -> tuple[int, int, int]:
 
 STAT_NAMES = (["lane_batches", "lane_cycles", "first_batches", "first_cycles"] +
               [f"mode{m}_{f}" for m in range(5) for f in ("steps", "cycles", "short_sum", "long_sum")] +
-              ["segments", "spilled_steps", "kernel_warp_cycles", "staged_gen_cycles", "staged_select_cycles",
-               "staged_chunks", "staged_windows", "staged_searches"])
+              ["segments", "spilled_steps", "kernel_warp_cycles", "staged_chunks", "staged_windows",
+               "staged_searches", "unused30", "unused31"])
 
 
 def n2v_step_stats(reset: bool = True) -> dict | None:
