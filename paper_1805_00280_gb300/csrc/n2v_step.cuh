@@ -694,7 +694,7 @@ struct MergeOut {
   int timed_out;
 };
 
-static __device__ __noinline__ MergeOut merge_step_ool(GraphView g, StepCtx c, WarpSmem sm, uint64_t u, uint32_t a_p,
+__device__ __noinline__ MergeOut merge_step_ool(GraphView g, StepCtx c, WarpSmem sm, uint64_t u, uint32_t a_p,
                                                 uint32_t a_q, int lane) {
   c.g = &g;
   MergeOut o;
