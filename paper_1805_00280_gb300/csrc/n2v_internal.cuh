@@ -121,14 +121,12 @@ struct LaunchCfg {
   int merge_ratio;     // x10, merge form of short steps (0: off)
 };
 
-// Shared memory of one warp: four mbarrier slots (32 bytes), the cached
-// reciprocal of a_q (16 bytes), the specials buffer (smem_specials uint32),
-// then stage_buffers staging windows of stage_window + 8 int32 each (16-byte
-// aligned).
-constexpr int kWarpSmemHeader = 48;
+// Shared memory of one warp: four mbarrier slots (32 bytes), the specials
+// buffer (smem_specials uint32), then stage_buffers staging windows of
+// stage_window + 8 int32 each (16-byte aligned).
 __host__ __device__ __forceinline__ int warp_smem_bytes(const LaunchCfg& c) {
   const int win = c.stage_window > 0 ? c.stage_buffers * (c.stage_window + 8) * 4 : 0;
-  return kWarpSmemHeader + c.smem_specials * 4 + win;
+  return 32 + c.smem_specials * 4 + win;
 }
 
 // ---------------------------------------------------------------------------

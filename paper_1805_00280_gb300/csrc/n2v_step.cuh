@@ -95,22 +95,20 @@ struct WarpSmem {
   uint32_t parity;   // bit b: parity of the next phase of bar[b]
   bool timed_out;    // a bounded wait gave up
   int merge_ratio;   // x10: merge both lists when deg v + deg t <= merge_ratio/10 * the probe cost (0: never)
-  unsigned long long* inv;  // shared: [0] the a_q of the cached reciprocal (0: none yet), [1] the reciprocal
+  uint32_t inv_q;    // the a_q that aq_inv belongs to (0: none yet)
+  uint64_t aq_inv;   // floor((2^64 - 1) / inv_q)
 };
 
-// floor(x / d) by a multiply with the reciprocal floor((2^64 - 1) / d), kept
-// in the warp's shared memory (not in registers): the estimate umulhi(x, inv)
-// is floor(x / d) or one less, and one comparison corrects it.  The reciprocal
-// is computed once per warp and value of d (d is uniform in the warp; every
-// lane computes and stores the same values).
+// floor(x / d) for d = sm.inv_q, by a multiply with the cached reciprocal
+// floor((2^64 - 1) / d): the estimate umulhi(x, inv) is floor(x / d) or one
+// less, and one comparison corrects it.  The reciprocal is computed once per
+// warp and value of d (uniform in the warp).
 __device__ __forceinline__ uint64_t div_aq(WarpSmem& sm, uint64_t x, uint32_t d) {
-  uint64_t rec = sm.inv[1];
-  if (sm.inv[0] != (unsigned long long)d) {
-    rec = ~0ull / (uint64_t)d;
-    sm.inv[1] = rec;
-    sm.inv[0] = d;
+  if (sm.inv_q != d) {
+    sm.inv_q = d;
+    sm.aq_inv = ~0ull / (uint64_t)d;
   }
-  uint64_t q = __umul64hi(x, rec);
+  uint64_t q = __umul64hi(x, sm.aq_inv);
   if (x - q * (uint64_t)d >= (uint64_t)d) ++q;
   return q;
 }
@@ -119,10 +117,9 @@ __device__ __forceinline__ WarpSmem warp_smem(unsigned char* base, int warp, con
   WarpSmem w;
   unsigned char* p = base + (size_t)warp * warp_smem_bytes(L);
   w.bar = (uint64_t*)p;
-  w.inv = (unsigned long long*)(p + 32);
-  w.spec = (uint32_t*)(p + kWarpSmemHeader);
+  w.spec = (uint32_t*)(p + 32);
   w.cap = L.smem_specials;
-  w.win = (int32_t*)(p + kWarpSmemHeader + L.smem_specials * 4);
+  w.win = (int32_t*)(p + 32 + L.smem_specials * 4);
   w.wlen = L.stage_window;
   w.nbuf = L.stage_buffers;
   w.spill = spill;
@@ -130,15 +127,13 @@ __device__ __forceinline__ WarpSmem warp_smem(unsigned char* base, int warp, con
   w.parity = 0;
   w.timed_out = false;
   w.merge_ratio = L.stage_window > 0 ? L.merge_ratio : 0;
+  w.inv_q = 0;
+  w.aq_inv = 0;
   return w;
 }
 
-// Initialise this warp's mbarriers and reciprocal cache (once per kernel, whole warp).
+// Initialise this warp's mbarriers (once per kernel, whole warp).
 __device__ __forceinline__ void warp_smem_init(WarpSmem& w, int lane) {
-  if (lane == 0) {
-    w.inv[0] = 0ull;
-    w.inv[1] = 0ull;
-  }
   if (w.wlen > 0 && lane == 0) {
     for (int b = 0; b < w.nbuf; ++b) mbar_init(&w.bar[b], 1);
     fence_mbar_init();
@@ -685,33 +680,6 @@ __device__ __forceinline__ int32_t merge_step(const StepCtx& c, WarpSmem& sm, ui
   return lds32(A + 4u * (uint32_t)chosen);
 }
 
-// The merge form out of line: its registers do not weigh on the inlined steps
-// around it (it is off by default).  Arguments by value; the staging state it
-// changes comes back in the result.
-struct MergeOut {
-  int32_t x;
-  uint32_t parity;
-  int timed_out;
-};
-
-__device__ __noinline__ MergeOut merge_step_ool(GraphView g, StepCtx c, WarpSmem sm, uint64_t u, uint32_t a_p,
-                                                uint32_t a_q, int lane) {
-  c.g = &g;
-  MergeOut o;
-  o.x = merge_step(c, sm, u, a_p, a_q, lane);
-  o.parity = sm.parity;
-  o.timed_out = sm.timed_out ? 1 : 0;
-  return o;
-}
-
-__device__ __forceinline__ int32_t merge_call(const GraphView& g, const StepCtx& c, WarpSmem& sm, uint64_t u,
-                                              uint32_t a_p, uint32_t a_q, int lane) {
-  const MergeOut o = merge_step_ool(g, c, sm, u, a_p, a_q, lane);
-  sm.parity = o.parity;
-  sm.timed_out = sm.timed_out || o.timed_out != 0;
-  return o.x;
-}
-
 // How a step enumerates its specials (the generator modes of gen_specials) and
 // which hub structure, if any, serves its longer list.
 struct StepPlan {
@@ -975,7 +943,7 @@ __device__ __forceinline__ int32_t warp_step(const GraphView& g, int64_t t, int6
   };
 #endif
   if (pl.mode == 4) {
-    const int32_t x = merge_call(g, c, sm, u, a_p, a_q, lane);
+    const int32_t x = merge_step(c, sm, u, a_p, a_q, lane);
 #ifdef N2V_STATS
     stat();
 #endif
@@ -1024,7 +992,7 @@ __device__ __forceinline__ int32_t block_step(const GraphView& g, int64_t t, int
   const int64_t bt = g.rp[t], et = g.rp[t + 1];
   StepCtx c = step_ctx(g, t, bv, ev, bt, et);
   StepPlan pl = plan_step(c, g, t, v, sm, stream_ratio, sm.merge_ratio);
-  if (pl.mode == 4) return merge_call(g, c, sm, u, a_p, a_q, lane);  // short lists: every warp merges them alike
+  if (pl.mode == 4) return merge_step(c, sm, u, a_p, a_q, lane);  // short lists: every warp merges them alike
   const bool cand_v = pl.mode == 0 || pl.mode == 3;  // candidates: N(v) (positions) or S
   if (!cand_v) find_t_slot(c);
   const int nc = cand_v ? c.dv : c.slen;
