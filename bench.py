@@ -180,15 +180,16 @@ def measured_peak_hbm():
 
 
 def ncu_traffic(workload: str, variant: str, tune: dict):
-    """Per-launch DRAM bytes from a committed ncu summary, if neither the kernels nor the tuning have changed since."""
+    """Per-launch DRAM bytes from a committed ncu summary of this workload and variant, if the kernel
+    sources have not changed since; with whether the run's tuning is the one it was captured with."""
     p = os.path.join(REPO, "profiles", f"traffic_{variant}_{workload}.json")
     try:
         d = json.load(open(p))
     except Exception:
-        return None
-    if d.get("csrc_sha") != csrc_digest() or d.get("tune") != tune:
-        return None
-    return d.get("dram_bytes_per_launch")
+        return None, None
+    if d.get("csrc_sha") != csrc_digest():
+        return None, None
+    return d.get("dram_bytes_per_launch"), d.get("tune") == tune
 
 
 # --------------------------------------------------------------------------
@@ -427,9 +428,11 @@ def run_ours(args):
     # ---- roofline of the dominant kernel (the persistent sampler: one launch per (p,q))
     peak, peak_kind = measured_peak_hbm()
     achieved = sum(abytes) / (sum(mean_launch_ms) / 1e3) / 1e9
-    dram = ncu_traffic(wl.name, args.variant, tune.as_dict())
+    dram, dram_same_tune = ncu_traffic(wl.name, args.variant, tune.as_dict())
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": dram, "peak_kind": peak_kind,
+                "traffic": dram, "traffic_same_tuning": dram_same_tune,
+                "traffic_source": f"profiles/traffic_{args.variant}_{wl.name}.json" if dram else None,
+                "peak_kind": peak_kind,
                 "algorithmic_bytes_per_launch": [int(b) for b in abytes],
                 "kernel": {"persistent": "k_persistent", "binned": "k_binned_step", "plain": "k_plain_step"}[args.variant],
                 "bytes_model": "16 + 4 deg(v) (1+weighted) + [k>=1](16 + 4 deg(t)) + 4 per real transition"}
@@ -953,12 +956,13 @@ def stored_compare(n2v, graph, g, starts, n_start, r_total, l, pq, seed, walk_be
 
 
 def ingest_ncu(csv_path: str, json_path: str, out_dir: str | None = None) -> str:
-    """Per-launch DRAM traffic of the timed launches, from a one-pass ncu launch list.
+    """Per-call DRAM traffic of the timed sampler launches, from a one-pass ncu launch list.
 
-    The run must be ``bench.py ... --no-cpu --no-e2e`` (one variant timed, then the
-    compared variants with the timed one first): its sampler launches are the
-    autotuner's, then warm-up x jobs, then steps x jobs (timed), then two per job
-    for the comparison.
+    The run must be ``bench.py ... --no-cpu --no-e2e --compare none --c2 0`` (one variant timed,
+    nothing after the timed region but the traffic counters), captured with
+    ``--metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum``.  Its last
+    steps x len(pq) x chunks sampler launches are the timed ones; one timed unit (the roofline's
+    "launch") is one n2v_walk call, i.e. ``chunks`` kernel launches, and its traffic is their sum.
     """
     import csv
 
@@ -967,6 +971,8 @@ def ingest_ncu(csv_path: str, json_path: str, out_dir: str | None = None) -> str
     cfg = d["config"]
     npq, steps = len(cfg["pq"]), d["steps"]
     kernel = d["roofline"]["kernel"]
+    chunk = cfg["tune"].get("chunk_walkers", 0)
+    per_call = -(-cfg["walks_per_gpu"] // chunk) if chunk > 0 and cfg["variant"] == "persistent" else 1
     rows = list(csv.reader(open(csv_path)))
     hi = next(i for i, r in enumerate(rows) if "Metric Name" in r)
     h = rows[hi]
@@ -976,17 +982,20 @@ def ingest_ncu(csv_path: str, json_path: str, out_dir: str | None = None) -> str
         if len(r) > MV and kernel in r[K]:
             by.setdefault(int(r[I]), {})[r[MN]] = float(r[MV].replace(",", ""))
     launches = [by[i] for i in sorted(by)]
-    timed = launches[-(2 + steps) * npq: -2 * npq]
-    traffic = [x["dram__bytes_read.sum"] + x["dram__bytes_write.sum"] for x in timed]
+    timed = launches[-steps * npq * per_call:]
+    calls = [timed[c * per_call:(c + 1) * per_call] for c in range(steps * npq)]
+    traffic = [sum(x["dram__bytes_read.sum"] + x["dram__bytes_write.sum"] for x in c) for c in calls]
     out = {"workload": cfg["workload"], "variant": cfg["variant"], "kernel": kernel, "csrc_sha": csrc_digest(),
-           "tune": cfg["tune"], "pq": cfg["pq"], "walks_per_launch": cfg["walks_per_gpu"],
+           "tune": cfg["tune"], "pq": cfg["pq"], "walks_per_call": cfg["walks_per_gpu"],
+           "kernel_launches_per_call": per_call,
            "dram_bytes_per_launch": int(statistics.mean(traffic)),
-           "per_launch": [{"dram_read": int(x["dram__bytes_read.sum"]), "dram_write": int(x["dram__bytes_write.sum"]),
-                           "ncu_ms": x["gpu__time_duration.sum"] / 1e6} for x in timed],
+           "per_call": [{"dram_read": int(sum(x["dram__bytes_read.sum"] for x in c)),
+                         "dram_write": int(sum(x["dram__bytes_write.sum"] for x in c)),
+                         "ncu_ms": sum(x["gpu__time_duration.sum"] for x in c) / 1e6} for c in calls],
            "algorithmic_bytes_per_launch": d["roofline"]["algorithmic_bytes_per_launch"],
            "source": "ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum "
-                     "--clock-control none (one pass), timed launches of bench.py --steps %d --warmup %d "
-                     "--no-cpu --no-e2e" % (steps, d["warmup"])}
+                     "--clock-control none (one pass), the timed launches of bench.py --workload %s --steps %d "
+                     "--warmup %d --no-cpu --no-e2e --compare none --c2 0" % (cfg["workload"], steps, d["warmup"])}
     p = os.path.join(out_dir or os.path.join(REPO, "profiles"), f"traffic_{cfg['variant']}_{cfg['workload']}.json")
     with open(p, "w") as f:
         json.dump(out, f, indent=1)

@@ -17,24 +17,43 @@ def write_launch_list(path, kernels):
 
 
 def test_ingest_picks_the_timed_launches(tmp_path):
+    """One n2v_walk call per (p, q); nothing but the traffic counters after the timed steps."""
     K = "void n2v::k_persistent<5>(n2v::GraphView, ...)"
     npq, warmup, steps = 3, 3, 1
     launches = [(K, 10, 1, 1)] * 4  # autotuner
     launches += [("n2v::k_validate_stats", 5, 0, 0)]
     launches += [(K, 100 + i, 7, 1) for i in range(warmup * npq)]  # warm-up
-    launches += [(K, 200 + i, 1000 * (i + 1), 10 * (i + 1)) for i in range(steps * npq)]  # timed
     launches += [("at::fill", 1, 0, 0)]
-    launches += [(K, 50, 3, 3)] * (2 * npq)  # comparison: untimed + timed per job
-    launches += [("n2v::k_plain_step", 9, 0, 0)] * 20
+    launches += [(K, 200 + i, 1000 * (i + 1), 10 * (i + 1)) for i in range(steps * npq)]  # timed
+    launches += [("n2v::k_traffic", 9, 0, 0)] * npq
     write_launch_list(tmp_path / "l.csv", launches)
     line = {"steps": steps, "warmup": warmup,
             "config": {"pq": [[1, 1], [0.25, 4], [4, 0.25]], "workload": "testwl", "variant": "persistent",
-                       "tune": {"blocks_per_sm": 5}, "walks_per_gpu": 64},
+                       "tune": {"blocks_per_sm": 5, "chunk_walkers": 0}, "walks_per_gpu": 64},
             "roofline": {"kernel": "k_persistent", "algorithmic_bytes_per_launch": [1, 2, 3]}}
     (tmp_path / "b.json").write_text("some log line\n" + json.dumps(line) + "\n")
     p = bench.ingest_ncu(str(tmp_path / "l.csv"), str(tmp_path / "b.json"), str(tmp_path))
     d = json.load(open(p))
-    assert [x["dram_read"] for x in d["per_launch"]] == [1000, 2000, 3000]
-    assert [x["dram_write"] for x in d["per_launch"]] == [10, 20, 30]
+    assert d["kernel_launches_per_call"] == 1
+    assert [x["dram_read"] for x in d["per_call"]] == [1000, 2000, 3000]
+    assert [x["dram_write"] for x in d["per_call"]] == [10, 20, 30]
     assert d["dram_bytes_per_launch"] == (1010 + 2020 + 3030) // 3
-    assert d["tune"] == {"blocks_per_sm": 5} and d["csrc_sha"] == bench.csrc_digest()
+    assert d["tune"] == {"blocks_per_sm": 5, "chunk_walkers": 0} and d["csrc_sha"] == bench.csrc_digest()
+
+
+def test_ingest_sums_the_chunk_launches_of_a_call(tmp_path):
+    """A call of 2^26 walks in 2^23-walk chunks is eight kernel launches: its traffic is their sum."""
+    K = "void n2v::k_persistent<5>(n2v::GraphView, ...)"
+    launches = [(K, 10, 1, 1)] * 5  # autotuner
+    launches += [(K, 100, 7, 7)] * 8  # warm-up call
+    launches += [(K, 200, 100 + i, 1) for i in range(8)]  # the timed call
+    launches += [("n2v::k_traffic", 9, 0, 0)]
+    write_launch_list(tmp_path / "l.csv", launches)
+    line = {"steps": 1, "warmup": 1,
+            "config": {"pq": [[2, 0.5]], "workload": "big", "variant": "persistent",
+                       "tune": {"chunk_walkers": 1 << 23}, "walks_per_gpu": 1 << 26},
+            "roofline": {"kernel": "k_persistent", "algorithmic_bytes_per_launch": [1]}}
+    (tmp_path / "b.json").write_text(json.dumps(line) + "\n")
+    d = json.load(open(bench.ingest_ncu(str(tmp_path / "l.csv"), str(tmp_path / "b.json"), str(tmp_path))))
+    assert d["kernel_launches_per_call"] == 8
+    assert d["dram_bytes_per_launch"] == sum(100 + i for i in range(8)) + 8
