@@ -352,6 +352,9 @@ def run_ours(args):
                                 wl.seed, sample=n_tune, stream=stream)
         tuned = {"tune": best.as_dict(), "sample_ms": round(ms, 3), "tune_s": round(time.perf_counter() - t0, 2)}
         tune = best
+    caches = None
+    if args.variant == "persistent":
+        caches = cache_ab(n2v, graph, tune, g, wl.l, pq[0][0], pq[0][1], wl.seed, stream, dev)
     info = graph.info()
     l = wl.l
     n_start = g.n
@@ -594,6 +597,7 @@ def run_ours(args):
             (-(-W // tune.chunk_walkers) if tune.chunk_walkers > 0 else 1) if args.variant == "persistent" else l),
         "clocks": clk,
         "compare": compare,
+        "hub_caches": caches,
         "c2": c2,
         "parity": parity,
         "wall_s_timed": wall,
@@ -803,6 +807,49 @@ def degree_bins(graph, info, rows) -> dict:
     vs = [int(x) for x in info.deg_hist]
     last = max([i for i in range(34) if vs[i]] + [0]) + 1
     return {"vertices": vs[:last], "visits": [int(x) for x in visits.cpu()][:last]}
+
+
+def cache_ab(n2v, graph, tune, g, l: int, p: float, q: float, seed: int, stream, dev) -> dict | None:
+    """The hub caches the graph was loaded with, each switched on over the chosen tuning and timed
+    on the autotuner's kind of sample (2^20 random start vertices, walks of up to 20 steps): the
+    measured evidence behind the tuner's choice.  None when no cache was loaded."""
+    import numpy as np
+    import torch
+
+    loaded = graph.tune_loaded
+    if loaded.hub_count <= 0 and loaded.bitmap_hubs <= 0:
+        return None
+    rng = np.random.default_rng(9)
+    sample = min(1 << 20, g.n)
+    starts = torch.from_numpy(rng.choice(g.n, size=sample, replace=False).astype(np.int32)).to(dev)
+    ls = min(l, 20)
+    out = torch.empty((sample, ls), dtype=torch.int32, device=dev)
+    base = tune.as_dict()
+    cands = [("chosen", {})]
+    if loaded.hub_count > 0:
+        cands.append(("hashed_sets", {"hub_count": loaded.hub_count, "hub_budget_mb": loaded.hub_budget_mb}))
+    if loaded.bitmap_hubs > 0:
+        cands.append(("rank_bitmaps", {"bitmap_hubs": loaded.bitmap_hubs}))
+    if loaded.hub_count > 0 and loaded.bitmap_hubs > 0:
+        cands.append(("both", {"hub_count": loaded.hub_count, "hub_budget_mb": loaded.hub_budget_mb,
+                               "bitmap_hubs": loaded.bitmap_hubs}))
+    res = {}
+    for name, over in cands:
+        t = n2v.default_tune(**{**base, **over})
+        graph.retune(t, stream)
+        info = graph.info()
+        n2v.walk(graph, starts, 1, ls, p, q, seed, "persistent", out=out, stream=stream)  # warm-up
+        best = None
+        for _ in range(2):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            n2v.walk(graph, starts, 1, ls, p, q, seed, "persistent", out=out, stream=stream)
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            best = a.elapsed_time(b) if best is None else min(best, a.elapsed_time(b))
+        res[name] = {"ms": round(best, 3), "hub_count": info.hub_count, "bitmap_hubs": info.bitmap_hubs}
+    graph.retune(tune, stream)
+    return {"sample_walks": sample, "l": ls, "candidates": res}
 
 
 def compare_ranges(W: int, n_start: int, args, wdef: dict) -> list[tuple[int, int]]:

@@ -415,6 +415,8 @@ class Graph:
         self.n = int(self.row_ptr.numel() - 1)
         self.nnz = int(self.col.numel())
         self.tune = tune if tune is not None else n2v_tune_default()
+        self.tune_loaded = n2v_tune()  # the tuning the aux buffer is laid out for
+        ctypes.pointer(self.tune_loaded)[0] = self.tune
         nbytes = n2v_graph_aux_bytes(self.n, self.nnz, self.w is not None, self.tune)
         self.aux = torch.empty(max(nbytes, 256) // 8 + 32, dtype=torch.int64, device=device)
         self.handle = n2v_graph_load(self.row_ptr, self.col, self.w, self.n, self.nnz, self.aux, self.tune,
