@@ -87,7 +87,7 @@ WORKLOAD_DEFAULTS = {
     "rmat22": {"tune": {"bitmap_hubs": 64, "hub_count": 4194, "hub_budget_mb": 2048}, "cuda_graph": 1},
     # the hub cache of the top 0.1% of vertices (2^23 / 1000 hashed sets) and 32 rank bitmaps;
     # the autotuner picks how many of each to keep
-    "rmat23w": {"tune": {"hub_count": 8388, "bitmap_hubs": 32}},
+    "rmat23w": {"tune": {"hub_count": 8388, "hub_budget_mb": 8192, "bitmap_hubs": 32}},
     "rmat20": {"tune": {"bitmap_hubs": 32}},
 }
 
