@@ -116,6 +116,11 @@ typedef struct n2v_tune {
                               a merge of the two lists in shared memory (each lane one segment
                               of the merge path) when deg v + deg t <= merge_ratio/10 *
                               32*ceil(short/32) * log2(long); 0 = never                     */
+  int32_t l2_persist_mb;   /* MiB at the start of col that the persistent sampler's launches mark
+                              as persisting in L2 (an access-policy window; the context's
+                              persisting set-aside is raised to match, up to the device's
+                              maximum).  On degree-ordered vertex ids the start of col holds the
+                              largest hubs' lists.  0 = off                                   */
   int32_t reserved[1];     /* must be zero                                                    */
 } n2v_tune;
 

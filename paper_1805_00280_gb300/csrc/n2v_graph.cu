@@ -367,7 +367,7 @@ static bool tune_ok(const n2v_tune& t) {
   if (t.smem_specials % 32) return false;
   if (t.stage_buffers != 2 && t.stage_buffers != 4) return false;
   if (t.bitmap_hubs < 0 || t.bitmap_hubs > 4096 || t.block_min_deg < 0) return false;
-  if (t.merge_ratio < 0 || t.merge_ratio > 1000000) return false;
+  if (t.merge_ratio < 0 || t.merge_ratio > 1000000 || t.l2_persist_mb < 0 || t.l2_persist_mb > 4096) return false;
   if (t.reserved[0]) return false;
   return true;
 }

@@ -119,6 +119,7 @@ struct LaunchCfg {
   int minb;            // persistent kernel instance: resident 128-thread blocks per SM it is compiled for
   int block_min_deg;   // persistent sampler: 0 = warps independent; > 0 = block batches with a block tier
   int merge_ratio;     // x10, merge form of short steps (0: off)
+  size_t l2_persist_bytes;  // bytes at the start of col marked persisting in L2 (0: off)
 };
 
 // Shared memory of one warp: four mbarrier slots (32 bytes), the specials

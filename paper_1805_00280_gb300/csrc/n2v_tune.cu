@@ -110,6 +110,7 @@ int n2v_autotune(n2v_graph* g, const int32_t* starts, int64_t n_starts, int32_t 
   }
   axes.push_back({&n2v_tune::stream_ratio, {15, 40, 100}});
   axes.push_back({&n2v_tune::merge_ratio, {0, 3, 10}});
+  axes.push_back({&n2v_tune::l2_persist_mb, {0, 32, 64}});
   axes.push_back({&n2v_tune::thread_max_deg, {0, 16, 48}});
   axes.push_back({&n2v_tune::stage_buffers, {2, 4}});
   axes.push_back({&n2v_tune::smem_specials, {256, 128, 512}});

@@ -291,8 +291,40 @@ static const void* persistent_fn(int minb, bool blk) {
   }
 }
 
+// A launch of kernel `k` that marks the first L.l2_persist_bytes of col as
+// persisting in L2 (access-policy window; the rest of the kernel's accesses
+// stream as usual).
+template <typename K>
+static void launch_persisting(K k, const LaunchCfg& L, int smem, cudaStream_t s, const GraphView& g, const WalkJob& J,
+                              unsigned long long* counter, uint32_t* spill) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeAccessPolicyWindow;
+  attr[0].val.accessPolicyWindow.base_ptr = (void*)g.col;
+  attr[0].val.accessPolicyWindow.num_bytes = L.l2_persist_bytes;
+  attr[0].val.accessPolicyWindow.hitRatio = 1.0f;
+  attr[0].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+  attr[0].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)L.blocks);
+  cfg.blockDim = dim3((unsigned)L.block_threads);
+  cfg.dynamicSmemBytes = (size_t)smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k, g, J, counter, L, spill);
+}
+
 static void launch_persistent(const LaunchCfg& L, int smem, cudaStream_t s, const GraphView& g, const WalkJob& J,
                               unsigned long long* counter, uint32_t* spill) {
+  if (L.l2_persist_bytes > 0 && L.block_min_deg == 0) {
+    switch (L.minb) {
+      case 4: launch_persisting(k_persistent<4>, L, smem, s, g, J, counter, spill); break;
+      case 6: launch_persisting(k_persistent<6>, L, smem, s, g, J, counter, spill); break;
+      case 8: launch_persisting(k_persistent<8>, L, smem, s, g, J, counter, spill); break;
+      default: launch_persisting(k_persistent<5>, L, smem, s, g, J, counter, spill); break;
+    }
+    return;
+  }
   if (L.block_min_deg > 0) {
     switch (L.minb) {
       case 4: k_persistent_blk<4><<<L.blocks, L.block_threads, smem, s>>>(g, J, counter, L, spill); break;
@@ -310,6 +342,31 @@ static void launch_persistent(const LaunchCfg& L, int smem, cudaStream_t s, cons
   }
 }
 
+// The persisting L2 window over the start of col: the tuning's size, capped by
+// the device's largest window and by col itself.  The context's persisting
+// set-aside is raised to the window once per device (a limit of this process's
+// context, gone with it).  Returns 0 when the device offers none.
+static std::mutex g_l2_mu;
+static size_t g_l2_set[64];
+
+static size_t l2_persist_window(const n2v_graph* g) {
+  int max_win = 0, max_persist = 0;
+  if (cudaDeviceGetAttribute(&max_win, cudaDevAttrMaxAccessPolicyWindowSize, g->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, g->device) != cudaSuccess)
+    return 0;
+  size_t bytes = (size_t)g->tune.l2_persist_mb << 20;
+  bytes = std::min(bytes, (size_t)max_win);
+  bytes = std::min(bytes, (size_t)max_persist);
+  bytes = std::min(bytes, sizeof(int32_t) * (size_t)g->nnz);
+  if (bytes == 0 || g->device < 0 || g->device >= 64) return 0;
+  std::lock_guard<std::mutex> lock(g_l2_mu);
+  if (g_l2_set[g->device] < bytes) {
+    if (cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, bytes) != cudaSuccess) return 0;
+    g_l2_set[g->device] = bytes;
+  }
+  return bytes;
+}
+
 LaunchCfg resolve_launch(const n2v_graph* g, int variant) {
   LaunchCfg c{};
   c.block_threads = g->tune.block_threads;
@@ -321,6 +378,8 @@ LaunchCfg resolve_launch(const n2v_graph* g, int variant) {
   c.stage_buffers = g->tune.stage_buffers;
   c.merge_ratio = g->tune.merge_ratio;
   c.block_min_deg = 0;
+  c.l2_persist_bytes = 0;
+  if (g->tune.l2_persist_mb > 0 && variant == N2V_PERSISTENT) c.l2_persist_bytes = l2_persist_window(g);
   if (variant == N2V_PERSISTENT) {
     // 128-thread blocks; the tuning's resident warps per SM (20 by default),
     // as many as shared memory holds

@@ -50,7 +50,7 @@ class n2v_tune(ctypes.Structure):
                 ("stage_window", ctypes.c_int32), ("stream_ratio", ctypes.c_int32),
                 ("spill_specials", ctypes.c_int32), ("stage_buffers", ctypes.c_int32),
                 ("bitmap_hubs", ctypes.c_int32), ("block_min_deg", ctypes.c_int32),
-                ("merge_ratio", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
+                ("merge_ratio", ctypes.c_int32), ("l2_persist_mb", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}

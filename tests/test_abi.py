@@ -94,7 +94,8 @@ def test_host_argument_checks_need_no_gpu():
                                          ("stage_window", 100), ("stage_window", 8192), ("stage_buffers", 3),
                                          ("smem_specials", 48), ("smem_specials", 16), ("stream_ratio", -1),
                                          ("blocks_per_sm", -1), ("hub_budget_mb", -1), ("bitmap_hubs", -1),
-                                         ("bitmap_hubs", 4097), ("block_min_deg", -1), ("merge_ratio", -1)])
+                                         ("bitmap_hubs", 4097), ("block_min_deg", -1), ("merge_ratio", -1),
+                                         ("l2_persist_mb", -1), ("l2_persist_mb", 5000)])
 def test_tune_validation_rejects(field, value):
     t = n2v.n2v_tune_default()
     setattr(t, field, value)
@@ -105,7 +106,7 @@ def test_tune_validation_rejects(field, value):
 @pytest.mark.parametrize("field,value", [("block_threads", 64), ("block_threads", 256), ("stage_window", 0),
                                          ("stage_window", 4096), ("stage_buffers", 4), ("blocks_per_sm", 8),
                                          ("bitmap_hubs", 64), ("block_min_deg", 1), ("block_min_deg", 1 << 30),
-                                         ("merge_ratio", 0), ("merge_ratio", 1000)])
+                                         ("merge_ratio", 0), ("merge_ratio", 1000), ("l2_persist_mb", 64)])
 def test_tune_validation_accepts(field, value):
     t = n2v.n2v_tune_default()
     setattr(t, field, value)

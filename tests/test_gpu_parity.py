@@ -54,6 +54,8 @@ TUNES = {
     "merge_w64": dict(thread_max_deg=0, merge_ratio=1_000_000, stage_window=64),
     "merge_off": dict(thread_max_deg=0, merge_ratio=0),
     "block_merge": dict(thread_max_deg=0, merge_ratio=1_000_000, block_min_deg=1, stage_window=64),
+    # the persistent sampler's launches with a persisting L2 window over the start of col
+    "l2persist": dict(l2_persist_mb=8),
 }
 
 
@@ -183,7 +185,8 @@ def test_rmat14_full_output(weighted, pq):
     want = oracle_rows(g, starts, 20, p, q, 77, np.arange(g.n * 2))
     for tname in ["default", "hubs", "spill", "probe", "stage", "stage4", "segments", "warps16", "warps24", "warps32",
                   "bitmaps", "bitmaps_segments", "block_all", "block_none", "block_stage", "block_probe",
-                  "block_segments", "block_bitmaps", "merge_all", "merge_w64", "merge_off", "block_merge"]:
+                  "block_segments", "block_bitmaps", "merge_all", "merge_w64", "merge_off", "block_merge",
+                  "l2persist"]:
         graph = n2v.Graph.from_csr(g, tune=n2v.default_tune(**TUNES[tname]))
         for v in VARIANTS:
             got = gpu_rows(g, starts, 2, 20, p, q, 77, v, graph=graph)
