@@ -688,6 +688,9 @@ struct StepPlan {
 };
 
 // Identical in every lane (and in every warp of a block that shares the step).
+// FULL = false: the instance without hub caches and without the merge form
+// (those generators are then not compiled into the caller at all).
+template <bool FULL = true>
 __device__ __forceinline__ StepPlan plan_step(StepCtx& c, const GraphView& g, int64_t t, int64_t v,
                                               const WarpSmem& sm, int stream_ratio, int merge_ratio) {
   const bool v_short = c.dv <= c.slen;
@@ -700,11 +703,11 @@ __device__ __forceinline__ StepPlan plan_step(StepCtx& c, const GraphView& g, in
   // a longer list with a rank bitmap or a hashed set is always probed: about one load per
   // candidate instead of a search
   const int64_t lv = v_short ? t : v;
-  if (g.bm_data && longer >= g.bm_min_deg) pl.bm = bm_find(g, (int32_t)lv);
-  if (pl.bm < 0 && g.hub_of && longer >= g.hub_min_deg) pl.hub = __ldg(g.hub_of + lv);
+  if (FULL && g.bm_data && longer >= g.bm_min_deg) pl.bm = bm_find(g, (int32_t)lv);
+  if (FULL && pl.bm < 0 && g.hub_of && longer >= g.hub_min_deg) pl.hub = __ldg(g.hub_of + lv);
   if (pl.bm >= 0 || pl.hub >= 0) {
     pl.mode = v_short ? 0 : 1;
-  } else if (merge_ratio > 0 && c.dv <= sm.wlen && c.dt <= sm.wlen &&
+  } else if (FULL && merge_ratio > 0 && c.dv <= sm.wlen && c.dt <= sm.wlen &&
              (int64_t)(c.dv + c.dt) * 10 <= (int64_t)merge_ratio * probe_cost) {
     pl.mode = 4;  // both lists fit a window: merge them
   } else if (sm.wlen > 0 && longer > 64 && longer * 10 <= (int64_t)stream_ratio * probe_cost) {
@@ -914,6 +917,7 @@ __device__ __forceinline__ StepCtx step_ctx(const GraphView& g, int64_t t, int64
 }
 
 // bv, ev: row bounds of v; bt, et: row bounds of t (k >= 1)
+template <bool FULL = true>
 __device__ __forceinline__ int32_t warp_step(const GraphView& g, int64_t t, int64_t v, int64_t bv, int64_t ev,
                                              int64_t bt, int64_t et, int k, uint64_t u, uint32_t a_p, uint32_t a_q,
                                              WarpSmem& sm, int stream_ratio, int lane) {
@@ -930,7 +934,7 @@ __device__ __forceinline__ int32_t warp_step(const GraphView& g, int64_t t, int6
   const long long t_enter = clock64();
 #endif
   StepCtx c = step_ctx(g, t, bv, ev, bt, et);
-  const StepPlan pl = plan_step(c, g, t, v, sm, stream_ratio, sm.merge_ratio);
+  const StepPlan pl = plan_step<FULL>(c, g, t, v, sm, stream_ratio, sm.merge_ratio);
 #ifdef N2V_STATS
   auto stat = [&]() {
     if (lane == 0) {
@@ -942,7 +946,7 @@ __device__ __forceinline__ int32_t warp_step(const GraphView& g, int64_t t, int6
     }
   };
 #endif
-  if (pl.mode == 4) {
+  if (FULL && pl.mode == 4) {
     const int32_t x = merge_step(c, sm, u, a_p, a_q, lane);
 #ifdef N2V_STATS
     stat();
@@ -1096,7 +1100,9 @@ __device__ __forceinline__ bool approx_here(const WalkJob& J, int k, int64_t dv,
 // ---------------------------------------------------------------------------
 // One step for the 32 walkers a warp owns (one per lane).  Steps whose
 // degrees are all <= thr run on their own lane (thread bin); the others are
-// taken one after another by the whole warp (warp bin).
+// taken one after another by the whole warp (warp bin).  FULL = false: the
+// instance for exact walks without hub caches or the merge form.
+template <bool FULL = true>
 __device__ __forceinline__ int32_t warp_binned_step(const GraphView& g, bool alive, int64_t t, int64_t v, int k,
                                                     uint64_t wid, const WalkJob& J, int thr, WarpSmem& sm,
                                                     int stream_ratio, int lane) {
@@ -1118,7 +1124,7 @@ __device__ __forceinline__ int32_t warp_binned_step(const GraphView& g, bool ali
       et = g.rp[t + 1];
     }
     u = philox_draw(seed, wid, (uint32_t)k);
-    if (approx_here(J, k, ev - bv, et - bt)) {
+    if (FULL && approx_here(J, k, ev - bv, et - bt)) {
       small = true;  // taken on this lane, by static weights
       x = static_step(g, bv, ev, u);
     } else {
@@ -1141,7 +1147,7 @@ __device__ __forceinline__ int32_t warp_binned_step(const GraphView& g, bool ali
   while (wm) {
     const int src = __ffs(wm) - 1;
     wm &= wm - 1;
-    const int32_t xx = warp_step(g, __shfl_sync(kFull, t, src), __shfl_sync(kFull, v, src),
+    const int32_t xx = warp_step<FULL>(g, __shfl_sync(kFull, t, src), __shfl_sync(kFull, v, src),
                                  __shfl_sync(kFull, bv, src), __shfl_sync(kFull, ev, src),
                                  __shfl_sync(kFull, bt, src), __shfl_sync(kFull, et, src), k,
                                  __shfl_sync(kFull, u, src), a_p, a_q, sm, stream_ratio, lane);

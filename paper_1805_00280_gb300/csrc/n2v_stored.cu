@@ -201,7 +201,10 @@ __global__ void __launch_bounds__(256) k_stored_walk(GraphView g, const int64_t*
     if (s0 < 0 || s0 >= g.n) {
       atomicOr(J.status, kStInvalidArg);
     } else {
-      int64_t v = s0, e = -1, t = -1;
+      int64_t v = s0, e = -1;
+#ifdef N2V_CHECKED
+      int64_t t = -1;  // the previous vertex, for the checked build's total
+#endif
       for (; k < J.l; ++k) {
         const int64_t bv = __ldg(g.rp + v), dv = __ldg(g.rp + v + 1) - bv;
         if (dv == 0) break;
@@ -228,7 +231,9 @@ __global__ void __launch_bounds__(256) k_stored_walk(GraphView g, const int64_t*
         }
         N2V_CHECK(g, j >= 0 && j < dv);
         e = bv + j;
+#ifdef N2V_CHECKED
         t = v;
+#endif
         v = __ldg(g.col + e);
         row[k] = (int32_t)v;
       }

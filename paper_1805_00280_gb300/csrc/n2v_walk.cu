@@ -92,7 +92,10 @@ __global__ void __launch_bounds__(256) k_binned_step(GraphView g, WalkJob J, int
 // time from a device counter and runs them to the end; every step is binned
 // by degree as above.  Walkers are independent (FN-Multi's observation,
 // Section 3.4), so the order in which warps take them does not change any row.
-template <int MINB>
+// FULL = false is the lean instance: exact walks without hub caches or the
+// merge form, so that the step it inlines carries only the probe and staged
+// generators (fewer live registers, fewer spills).
+template <int MINB, bool FULL>
 __global__ void __launch_bounds__(kPersistThreads, MINB)
     k_persistent(GraphView g, WalkJob J, unsigned long long* __restrict__ counter, LaunchCfg L,
                  uint32_t* __restrict__ spill) {
@@ -127,8 +130,8 @@ __global__ void __launch_bounds__(kPersistThreads, MINB)
     int k = 0;
     for (; k < J.l; ++k) {
       if (sm.timed_out || !__any_sync(kFull, alive)) break;
-      const int32_t x = warp_binned_step(g, alive, t, v, k, (uint64_t)wid, J, L.thread_max_deg, sm, L.stream_ratio,
-                                         lane);
+      const int32_t x = warp_binned_step<FULL>(g, alive, t, v, k, (uint64_t)wid, J, L.thread_max_deg, sm,
+                                               L.stream_ratio, lane);
       N2V_CHECK(g, !alive || (x >= -1 && x < g.n));
       if (mine) row[k] = alive ? x : -1;
       if (alive) {
@@ -274,7 +277,7 @@ static int smem_per_block(const LaunchCfg& c) {
 // latency.
 static int persistent_minb(int per_sm) { return per_sm <= 4 ? 4 : per_sm <= 5 ? 5 : per_sm <= 6 ? 6 : 8; }
 
-static const void* persistent_fn(int minb, bool blk) {
+static const void* persistent_fn(int minb, bool blk, bool lean) {
   if (blk) {
     switch (minb) {
       case 4: return (const void*)k_persistent_blk<4>;
@@ -283,63 +286,55 @@ static const void* persistent_fn(int minb, bool blk) {
       default: return (const void*)k_persistent_blk<5>;
     }
   }
+  if (lean) {
+    switch (minb) {
+      case 4: return (const void*)k_persistent<4, false>;
+      case 6: return (const void*)k_persistent<6, false>;
+      case 8: return (const void*)k_persistent<8, false>;
+      default: return (const void*)k_persistent<5, false>;
+    }
+  }
   switch (minb) {
-    case 4: return (const void*)k_persistent<4>;
-    case 6: return (const void*)k_persistent<6>;
-    case 8: return (const void*)k_persistent<8>;
-    default: return (const void*)k_persistent<5>;
+    case 4: return (const void*)k_persistent<4, true>;
+    case 6: return (const void*)k_persistent<6, true>;
+    case 8: return (const void*)k_persistent<8, true>;
+    default: return (const void*)k_persistent<5, true>;
   }
 }
 
-// A launch of kernel `k` that marks the first L.l2_persist_bytes of col as
-// persisting in L2 (access-policy window; the rest of the kernel's accesses
-// stream as usual).
-template <typename K>
-static void launch_persisting(K k, const LaunchCfg& L, int smem, cudaStream_t s, const GraphView& g, const WalkJob& J,
+// The instance a persistent launch takes: block batches when the block tier is
+// on; else the lean instance unless the call needs FN-Approx, the graph's view
+// carries a hub cache, or the merge form is on.
+static const void* persistent_fn(const LaunchCfg& L, const GraphView& g, const WalkJob& J) {
+  const bool blk = L.block_min_deg > 0;
+  const bool lean = !blk && !J.approx && L.merge_ratio == 0 && g.hub_of == nullptr && g.bm_data == nullptr;
+  return persistent_fn(L.minb, blk, lean);
+}
+
+// One persistent launch.  With L.l2_persist_bytes > 0 (warp batches only) the
+// first that many bytes of col are marked persisting in L2 (access-policy
+// window; the rest of the kernel's accesses stream as usual).
+static void launch_persistent(const LaunchCfg& L, int smem, cudaStream_t s, GraphView g, WalkJob J,
                               unsigned long long* counter, uint32_t* spill) {
+  LaunchCfg Lc = L;
+  void* args[] = {&g, &J, &counter, &Lc, &spill};
   cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeAccessPolicyWindow;
-  attr[0].val.accessPolicyWindow.base_ptr = (void*)g.col;
-  attr[0].val.accessPolicyWindow.num_bytes = L.l2_persist_bytes;
-  attr[0].val.accessPolicyWindow.hitRatio = 1.0f;
-  attr[0].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
-  attr[0].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)L.blocks);
   cfg.blockDim = dim3((unsigned)L.block_threads);
   cfg.dynamicSmemBytes = (size_t)smem;
   cfg.stream = s;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, k, g, J, counter, L, spill);
-}
-
-static void launch_persistent(const LaunchCfg& L, int smem, cudaStream_t s, const GraphView& g, const WalkJob& J,
-                              unsigned long long* counter, uint32_t* spill) {
   if (L.l2_persist_bytes > 0 && L.block_min_deg == 0) {
-    switch (L.minb) {
-      case 4: launch_persisting(k_persistent<4>, L, smem, s, g, J, counter, spill); break;
-      case 6: launch_persisting(k_persistent<6>, L, smem, s, g, J, counter, spill); break;
-      case 8: launch_persisting(k_persistent<8>, L, smem, s, g, J, counter, spill); break;
-      default: launch_persisting(k_persistent<5>, L, smem, s, g, J, counter, spill); break;
-    }
-    return;
+    attr[0].id = cudaLaunchAttributeAccessPolicyWindow;
+    attr[0].val.accessPolicyWindow.base_ptr = (void*)g.col;
+    attr[0].val.accessPolicyWindow.num_bytes = L.l2_persist_bytes;
+    attr[0].val.accessPolicyWindow.hitRatio = 1.0f;
+    attr[0].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+    attr[0].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
   }
-  if (L.block_min_deg > 0) {
-    switch (L.minb) {
-      case 4: k_persistent_blk<4><<<L.blocks, L.block_threads, smem, s>>>(g, J, counter, L, spill); break;
-      case 6: k_persistent_blk<6><<<L.blocks, L.block_threads, smem, s>>>(g, J, counter, L, spill); break;
-      case 8: k_persistent_blk<8><<<L.blocks, L.block_threads, smem, s>>>(g, J, counter, L, spill); break;
-      default: k_persistent_blk<5><<<L.blocks, L.block_threads, smem, s>>>(g, J, counter, L, spill); break;
-    }
-    return;
-  }
-  switch (L.minb) {
-    case 4: k_persistent<4><<<L.blocks, L.block_threads, smem, s>>>(g, J, counter, L, spill); break;
-    case 6: k_persistent<6><<<L.blocks, L.block_threads, smem, s>>>(g, J, counter, L, spill); break;
-    case 8: k_persistent<8><<<L.blocks, L.block_threads, smem, s>>>(g, J, counter, L, spill); break;
-    default: k_persistent<5><<<L.blocks, L.block_threads, smem, s>>>(g, J, counter, L, spill); break;
-  }
+  cudaLaunchKernelExC(&cfg, persistent_fn(L, g, J), args);
 }
 
 // The persisting L2 window over the start of col: the tuning's size, capped by
@@ -388,7 +383,7 @@ LaunchCfg resolve_launch(const n2v_graph* g, int variant) {
     const int warps = g->tune.blocks_per_sm > 0 ? g->tune.blocks_per_sm * (g->tune.block_threads / 32) : 20;
     int per_sm = std::max(1, (warps + 3) / 4);
     const int smem = smem_per_block(c);
-    const void* fn = persistent_fn(8, c.block_min_deg > 0);  // the fewest registers: only shared memory limits it
+    const void* fn = persistent_fn(8, c.block_min_deg > 0, false);  // the fewest registers: only shared memory limits it
     if (smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, c.block_threads, smem) == cudaSuccess && occ > 0)
@@ -471,7 +466,7 @@ static cudaError_t issue(const n2v_graph* g, const WalkCall& c, cudaStream_t s) 
   }
   // persistent
   if (smem > 48 * 1024)
-    cudaFuncSetAttribute(persistent_fn(L.minb, L.block_min_deg > 0), cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(persistent_fn(L, g->view, J), cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   const int64_t chunks = n_chunks(g, c.count);
   unsigned long long* counters = (unsigned long long*)c.ws;
   cudaError_t e = cudaMemsetAsync(counters, 0, sizeof(unsigned long long) * (size_t)chunks, s);
@@ -835,8 +830,6 @@ extern "C" int n2v_walk_noalloc(const n2v_graph* g, const int32_t* starts, int64
 
   LaunchCfg L = resolve_launch(g, N2V_PERSISTENT);
   const int smem = smem_per_block(L);
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute(persistent_fn(L.minb, L.block_min_deg > 0), cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   // the spill area is whatever the scratch has left, shared evenly by the warps
   const int64_t warps = (int64_t)L.blocks * (L.block_threads / 32);
   const int64_t per_warp = (int64_t)((kNoAllocScratchBytes - kNoAllocCounterBytes) / sizeof(uint32_t)) / warps;
@@ -861,6 +854,8 @@ extern "C" int n2v_walk_noalloc(const n2v_graph* g, const int32_t* starts, int64
   J.approx_popular = 0;
   J.w_min = g->info.w_min;
   J.w_max = g->info.w_max;
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(persistent_fn(L, g->view, J), cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   const int64_t per = chunks == 1 ? walk_count : g->tune.chunk_walkers;
   for (int64_t ci = 0; ci < chunks; ++ci) {
     const int64_t lo = ci * per;
