@@ -92,13 +92,23 @@ __global__ void __launch_bounds__(256) k_binned_step(GraphView g, WalkJob J, int
 // time from a device counter and runs them to the end; every step is binned
 // by degree as above.  Walkers are independent (FN-Multi's observation,
 // Section 3.4), so the order in which warps take them does not change any row.
-// FULL = false is the lean instance: exact walks without hub caches or the
-// merge form, so that the step it inlines carries only the probe and staged
-// generators (fewer live registers, fewer spills).
-template <int MINB, bool FULL>
+// KIND kPersistLean and kPersistLeanUnw are the lean instances: exact walks
+// without hub caches or the merge form, so that the step they inline carries
+// only the probe and staged generators (fewer live registers, fewer spills);
+// kPersistLeanUnw is for graphs without weights, which it knows at compile
+// time (g.w is null for such a graph, so setting it changes nothing but what
+// the compiler can fold).
+enum PersistKind { kPersistFull = 0, kPersistLean = 1, kPersistLeanUnw = 2 };
+
+template <int MINB, int KIND>
 __global__ void __launch_bounds__(kPersistThreads, MINB)
     k_persistent(GraphView g, WalkJob J, unsigned long long* __restrict__ counter, LaunchCfg L,
                  uint32_t* __restrict__ spill) {
+  constexpr bool FULL = KIND == kPersistFull;
+  if (KIND == kPersistLeanUnw) {
+    g.w = nullptr;
+    g.wpre = nullptr;
+  }
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
@@ -277,7 +287,7 @@ static int smem_per_block(const LaunchCfg& c) {
 // latency.
 static int persistent_minb(int per_sm) { return per_sm <= 4 ? 4 : per_sm <= 5 ? 5 : per_sm <= 6 ? 6 : 8; }
 
-static const void* persistent_fn(int minb, bool blk, bool lean) {
+static const void* persistent_fn(int minb, bool blk, int kind) {
   if (blk) {
     switch (minb) {
       case 4: return (const void*)k_persistent_blk<4>;
@@ -286,29 +296,38 @@ static const void* persistent_fn(int minb, bool blk, bool lean) {
       default: return (const void*)k_persistent_blk<5>;
     }
   }
-  if (lean) {
+  if (kind == kPersistLeanUnw) {
     switch (minb) {
-      case 4: return (const void*)k_persistent<4, false>;
-      case 6: return (const void*)k_persistent<6, false>;
-      case 8: return (const void*)k_persistent<8, false>;
-      default: return (const void*)k_persistent<5, false>;
+      case 4: return (const void*)k_persistent<4, kPersistLeanUnw>;
+      case 6: return (const void*)k_persistent<6, kPersistLeanUnw>;
+      case 8: return (const void*)k_persistent<8, kPersistLeanUnw>;
+      default: return (const void*)k_persistent<5, kPersistLeanUnw>;
+    }
+  }
+  if (kind == kPersistLean) {
+    switch (minb) {
+      case 4: return (const void*)k_persistent<4, kPersistLean>;
+      case 6: return (const void*)k_persistent<6, kPersistLean>;
+      case 8: return (const void*)k_persistent<8, kPersistLean>;
+      default: return (const void*)k_persistent<5, kPersistLean>;
     }
   }
   switch (minb) {
-    case 4: return (const void*)k_persistent<4, true>;
-    case 6: return (const void*)k_persistent<6, true>;
-    case 8: return (const void*)k_persistent<8, true>;
-    default: return (const void*)k_persistent<5, true>;
+    case 4: return (const void*)k_persistent<4, kPersistFull>;
+    case 6: return (const void*)k_persistent<6, kPersistFull>;
+    case 8: return (const void*)k_persistent<8, kPersistFull>;
+    default: return (const void*)k_persistent<5, kPersistFull>;
   }
 }
 
 // The instance a persistent launch takes: block batches when the block tier is
-// on; else the lean instance unless the call needs FN-Approx, the graph's view
-// carries a hub cache, or the merge form is on.
+// on; else a lean instance unless the call needs FN-Approx, the graph's view
+// carries a hub cache, or the merge form is on (the unweighted one for a graph
+// without weights).
 static const void* persistent_fn(const LaunchCfg& L, const GraphView& g, const WalkJob& J) {
   const bool blk = L.block_min_deg > 0;
   const bool lean = !blk && !J.approx && L.merge_ratio == 0 && g.hub_of == nullptr && g.bm_data == nullptr;
-  return persistent_fn(L.minb, blk, lean);
+  return persistent_fn(L.minb, blk, !lean ? kPersistFull : g.w ? kPersistLean : kPersistLeanUnw);
 }
 
 // One persistent launch.  With L.l2_persist_bytes > 0 (warp batches only) the
@@ -383,7 +402,7 @@ LaunchCfg resolve_launch(const n2v_graph* g, int variant) {
     const int warps = g->tune.blocks_per_sm > 0 ? g->tune.blocks_per_sm * (g->tune.block_threads / 32) : 20;
     int per_sm = std::max(1, (warps + 3) / 4);
     const int smem = smem_per_block(c);
-    const void* fn = persistent_fn(8, c.block_min_deg > 0, false);  // the fewest registers: only shared memory limits it
+    const void* fn = persistent_fn(8, c.block_min_deg > 0, kPersistFull);  // the fewest registers: only shared memory limits it
     if (smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, c.block_threads, smem) == cudaSuccess && occ > 0)
