@@ -122,6 +122,26 @@ struct LaunchCfg {
   size_t l2_persist_bytes;  // bytes at the start of col marked persisting in L2 (0: off)
 };
 
+// Instances of the persistent kernels.  The lean ones run exact walks without
+// hub caches or the merge form, so that the step they inline carries only the
+// probe and staged generators (fewer live registers, fewer spills);
+// kPersistLeanUnw is for graphs without weights and knows that at compile time.
+enum PersistKind { kPersistFull = 0, kPersistLean = 1, kPersistLeanUnw = 2 };
+
+// The instance an exact-walk launch under L over graph view g can take.
+__host__ __forceinline__ int persist_kind(const LaunchCfg& L, const GraphView& g) {
+  if (L.merge_ratio != 0 || g.hub_of != nullptr || g.bm_data != nullptr) return kPersistFull;
+  return g.w ? kPersistLean : kPersistLeanUnw;
+}
+
+// Inside a kPersistLeanUnw kernel: the view's weights are null already (the
+// host picks that instance only then); stating it lets the compiler drop the
+// weighted code paths.
+__device__ __forceinline__ void fold_unweighted(GraphView& g) {
+  g.w = nullptr;
+  g.wpre = nullptr;
+}
+
 // Shared memory of one warp: four mbarrier slots (32 bytes), the specials
 // buffer (smem_specials uint32), then stage_buffers staging windows of
 // stage_window + 8 int32 each (16-byte aligned).

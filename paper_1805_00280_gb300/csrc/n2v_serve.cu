@@ -35,10 +35,13 @@ struct DevSlice {
   uint32_t pad;
 };
 
-// 96 registers a thread: five resident 128-thread blocks per SM (the default grid)
+// 96 registers a thread: five resident 128-thread blocks per SM (the default
+// grid).  KIND: the full or a lean instance (PersistKind).
+template <int KIND>
 __global__ void __launch_bounds__(kPersistThreads, 5)
     k_serve(GraphView g, const DevSlice* __restrict__ slices, int nslices, int64_t total_slots,
             unsigned long long* __restrict__ counter, LaunchCfg L, uint32_t* __restrict__ spill, uint32_t* status) {
+  if (KIND == kPersistLeanUnw) fold_unweighted(g);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
@@ -80,7 +83,8 @@ __global__ void __launch_bounds__(kPersistThreads, 5)
       J.a_p = S.a_p;
       J.a_q = S.a_q;
       J.approx = 0;
-      const int32_t x = warp_binned_step(g, alive, t, v, k, (uint64_t)wid, J, L.thread_max_deg, sm, L.stream_ratio, lane);
+      const int32_t x = warp_binned_step<KIND == kPersistFull>(g, alive, t, v, k, (uint64_t)wid, J, L.thread_max_deg,
+                                                               sm, L.stream_ratio, lane);
       if (mine) row[k] = alive ? x : -1;
       if (alive) {
         if (x < 0) {
@@ -353,10 +357,12 @@ int n2v_serve_step(n2v_server* s, int* launched) {
   LaunchCfg L = resolve_launch(s->g, N2V_PERSISTENT);
   L.spill_specials = s->cfg.spill_specials;
   const int smem = (L.block_threads / 32) * warp_smem_bytes(L);
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k_serve, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  k_serve<<<L.blocks, L.block_threads, smem, s->stream>>>(s->g->view, (const DevSlice*)table,
-                                                          (int)s->host_slices.size(), slots, counter, L, spill,
-                                                          s->g->status);
+  const int kind = persist_kind(L, s->g->view);
+  auto kern = kind == kPersistLeanUnw ? k_serve<kPersistLeanUnw> : kind == kPersistLean ? k_serve<kPersistLean>
+                                                                                         : k_serve<kPersistFull>;
+  if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  kern<<<L.blocks, L.block_threads, smem, s->stream>>>(s->g->view, (const DevSlice*)table, (int)s->host_slices.size(),
+                                                       slots, counter, L, spill, s->g->status);
   if (cudaGetLastError() != cudaSuccess || cudaEventRecord(t.done, s->stream) != cudaSuccess) return N2V_ERR_CUDA;
   t.busy = true;
   s->cur ^= 1;

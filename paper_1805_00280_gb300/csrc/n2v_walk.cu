@@ -92,23 +92,13 @@ __global__ void __launch_bounds__(256) k_binned_step(GraphView g, WalkJob J, int
 // time from a device counter and runs them to the end; every step is binned
 // by degree as above.  Walkers are independent (FN-Multi's observation,
 // Section 3.4), so the order in which warps take them does not change any row.
-// KIND kPersistLean and kPersistLeanUnw are the lean instances: exact walks
-// without hub caches or the merge form, so that the step they inline carries
-// only the probe and staged generators (fewer live registers, fewer spills);
-// kPersistLeanUnw is for graphs without weights, which it knows at compile
-// time (g.w is null for such a graph, so setting it changes nothing but what
-// the compiler can fold).
-enum PersistKind { kPersistFull = 0, kPersistLean = 1, kPersistLeanUnw = 2 };
-
+// KIND selects the full or a lean instance (PersistKind).
 template <int MINB, int KIND>
 __global__ void __launch_bounds__(kPersistThreads, MINB)
     k_persistent(GraphView g, WalkJob J, unsigned long long* __restrict__ counter, LaunchCfg L,
                  uint32_t* __restrict__ spill) {
   constexpr bool FULL = KIND == kPersistFull;
-  if (KIND == kPersistLeanUnw) {
-    g.w = nullptr;
-    g.wpre = nullptr;
-  }
+  if (KIND == kPersistLeanUnw) fold_unweighted(g);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
@@ -326,8 +316,7 @@ static const void* persistent_fn(int minb, bool blk, int kind) {
 // without weights).
 static const void* persistent_fn(const LaunchCfg& L, const GraphView& g, const WalkJob& J) {
   const bool blk = L.block_min_deg > 0;
-  const bool lean = !blk && !J.approx && L.merge_ratio == 0 && g.hub_of == nullptr && g.bm_data == nullptr;
-  return persistent_fn(L.minb, blk, !lean ? kPersistFull : g.w ? kPersistLean : kPersistLeanUnw);
+  return persistent_fn(L.minb, blk, blk || J.approx ? kPersistFull : persist_kind(L, g));
 }
 
 // One persistent launch.  With L.l2_persist_bytes > 0 (warp batches only) the
