@@ -189,7 +189,18 @@ def ncu_traffic(workload: str, variant: str, tune: dict):
         return None, None
     if d.get("csrc_sha") != csrc_digest():
         return None, None
-    return d.get("dram_bytes_per_launch"), d.get("tune") == tune
+    return d.get("dram_bytes_per_launch"), effective_tune(d.get("tune")) == effective_tune(tune)
+
+
+def effective_tune(tune: dict | None) -> dict | None:
+    """The tuning as the persistent sampler runs it: blocks_per_sm 0 means its default of 20
+    resident warps per SM, i.e. five 128-thread blocks."""
+    if tune is None:
+        return None
+    t = dict(tune)
+    if t.get("blocks_per_sm", 0) <= 0:
+        t["blocks_per_sm"] = 5
+    return t
 
 
 # --------------------------------------------------------------------------

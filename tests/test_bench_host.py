@@ -57,3 +57,11 @@ def test_ingest_sums_the_chunk_launches_of_a_call(tmp_path):
     d = json.load(open(bench.ingest_ncu(str(tmp_path / "l.csv"), str(tmp_path / "b.json"), str(tmp_path))))
     assert d["kernel_launches_per_call"] == 8
     assert d["dram_bytes_per_launch"] == sum(100 + i for i in range(8)) + 8
+
+
+def test_traffic_tuning_compares_effective_tunings():
+    """A capture at the default 20 warps per SM (blocks_per_sm 0) matches a run whose tuner chose 5."""
+    a = {"blocks_per_sm": 0, "stream_ratio": 100}
+    assert bench.effective_tune(a) == bench.effective_tune({"blocks_per_sm": 5, "stream_ratio": 100})
+    assert bench.effective_tune(a) != bench.effective_tune({"blocks_per_sm": 4, "stream_ratio": 100})
+    assert bench.effective_tune(None) is None
