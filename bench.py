@@ -68,6 +68,9 @@ def parse_args():
                          "of a bench run with --no-cpu --no-e2e, and that run's JSON line")
     ap.add_argument("--cuda-graph", type=int, default=-1, help="record the launches as a CUDA graph (-1: per workload)")
     ap.add_argument("--autotune", type=int, default=1, help="tune the persistent sampler on a sample first")
+    ap.add_argument("--tune-cache", default="",
+                    help="directory of stored autotuner results: reuse the one for this graph, GPU, build and "
+                         "sample instead of tuning again (stored after a miss)")
     ap.add_argument("--jobs", type=int, default=10_000, help="serving workload: number of jobs")
     ap.add_argument("--load", type=float, default=0.8, help="serving: arrival rate as a fraction of capacity")
     return ap.parse_args()
@@ -359,9 +362,20 @@ def run_ours(args):
         # (R-MAT's first ids are its hubs: a prefix of the job would over-sample them)
         tune_starts = np.resize(np.arange(g.n, dtype=np.int32), n_tune) if n_tune == n_job else \
             np.arange(g.n, dtype=np.int32)
-        best, ms = n2v.autotune(graph, tune_starts, wl.l if n_tune == n_job else min(wl.l, 20), pq[0][0], pq[0][1],
-                                wl.seed, sample=n_tune, stream=stream)
+        l_tune = wl.l if n_tune == n_job else min(wl.l, 20)
+        from_cache = None
+        if args.tune_cache:
+            from paper_1805_00280_gb300 import tune_cache
+
+            best, ms, from_cache = tune_cache.autotune_cached(tune_cache.TuneCache(args.tune_cache), graph, g,
+                                                              tune_starts, l_tune, pq[0][0], pq[0][1], wl.seed,
+                                                              sample=n_tune, stream=stream)
+        else:
+            best, ms = n2v.autotune(graph, tune_starts, l_tune, pq[0][0], pq[0][1], wl.seed, sample=n_tune,
+                                    stream=stream)
         tuned = {"tune": best.as_dict(), "sample_ms": round(ms, 3), "tune_s": round(time.perf_counter() - t0, 2)}
+        if from_cache is not None:
+            tuned["cache"] = "hit" if from_cache else "miss"
         tune = best
     caches = None
     if args.variant == "persistent":
