@@ -15,7 +15,7 @@ What the key covers:
 
 A tuning never changes a row: the tunables choose how the work is scheduled, not what is
 computed. So a stale or colliding entry can cost speed but cannot change a walk. That is why the
-key may sample ``col`` instead of hashing all 8.6 GB of it on R-MAT 26.
+key may sample ``col`` instead of hashing all 8.4 GB of it on R-MAT 26.
 """
 from __future__ import annotations
 
