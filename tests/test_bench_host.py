@@ -65,3 +65,19 @@ def test_traffic_tuning_compares_effective_tunings():
     assert bench.effective_tune(a) == bench.effective_tune({"blocks_per_sm": 5, "stream_ratio": 100})
     assert bench.effective_tune(a) != bench.effective_tune({"blocks_per_sm": 4, "stream_ratio": 100})
     assert bench.effective_tune(None) is None
+
+
+def test_ingest_takes_every_instance_of_the_kernel(tmp_path):
+    """The lean instances' names carry a second template argument (with a comma)."""
+    K = "void n2v::k_persistent<5, 2>(n2v::GraphView, n2v::WalkJob, unsigned long long *, n2v::LaunchCfg, unsigned int *)"
+    launches = [(K, 100, 7, 7)] * 2  # warm-up call
+    launches += [(K, 200, 50 + i, 2) for i in range(2)]  # the timed call
+    write_launch_list(tmp_path / "l.csv", launches)
+    line = {"steps": 1, "warmup": 1,
+            "config": {"pq": [[2, 0.5]], "workload": "w", "variant": "persistent",
+                       "tune": {"chunk_walkers": 4}, "walks_per_gpu": 8},
+            "roofline": {"kernel": "k_persistent", "algorithmic_bytes_per_launch": [1]}}
+    (tmp_path / "b.json").write_text(json.dumps(line) + "\n")
+    d = json.load(open(bench.ingest_ncu(str(tmp_path / "l.csv"), str(tmp_path / "b.json"), str(tmp_path))))
+    assert d["kernel_launches_per_call"] == 2
+    assert d["dram_bytes_per_launch"] == 50 + 51 + 2 * 2
