@@ -292,9 +292,9 @@ int n2v_autotune_ws_bytes(const n2v_graph* g, int64_t sample, int32_t l, size_t*
 
 /* Pick the tuning of the persistent sampler for this graph and job shape:
  * a coordinate descent over stage_window, blocks_per_sm, stream_ratio,
- * merge_ratio, l2_persist_mb, thread_max_deg, stage_buffers, smem_specials,
- * block_min_deg and, from none up to the sizes the graph was loaded with,
- * bitmap_hubs and hub_count,
+ * merge_ratio, thread_max_deg, stage_buffers, smem_specials, block_min_deg
+ * and, from none up to the sizes the graph was loaded with, bitmap_hubs and
+ * hub_count (l2_persist_mb is left as given),
  * each candidate timed with CUDA events on walks [0, sample) of
  * the job "one walk from each of starts[0..sample)" (the caller should pass a
  * representative random sample of its start vertices).  A candidate is
