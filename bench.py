@@ -195,6 +195,15 @@ def ncu_traffic(workload: str, variant: str, tune: dict):
     return d.get("dram_bytes_per_launch"), effective_tune(d.get("tune")) == effective_tune(tune)
 
 
+def dram_fraction(dram_bytes_per_call, mean_call_ms: list, peak_gbs: float) -> dict | None:
+    """Measured DRAM bytes of one call (from an ncu capture) over the mean call time of this run:
+    the achieved DRAM bandwidth and its fraction of the peak (None without a capture)."""
+    if not dram_bytes_per_call or not mean_call_ms or sum(mean_call_ms) <= 0:
+        return None
+    gbs = dram_bytes_per_call * len(mean_call_ms) / (sum(mean_call_ms) / 1e3) / 1e9
+    return {"achieved": gbs, "unit": "GB/s", "frac": gbs / peak_gbs}
+
+
 def effective_tune(tune: dict | None) -> dict | None:
     """The tuning as the persistent sampler runs it: blocks_per_sm 0 means its default of 20
     resident warps per SM, i.e. five 128-thread blocks."""
@@ -464,6 +473,8 @@ def run_ours(args):
                 "algorithmic_bytes_per_launch": [int(b) for b in abytes],
                 "kernel": {"persistent": "k_persistent", "binned": "k_binned_step", "plain": "k_plain_step"}[args.variant],
                 "bytes_model": "16 + 4 deg(v) (1+weighted) + [k>=1](16 + 4 deg(t)) + 4 per real transition"}
+    # what the committed ncu capture's DRAM bytes come to over this run's call times
+    roofline["dram"] = dram_fraction(dram, mean_launch_ms, peak)
     # the conservative lower model: N(v) and the output only, no N(t) message
     lower_achieved = sum(lbytes) / (sum(mean_launch_ms) / 1e3) / 1e9
     roofline["lower_model"] = {"bytes_model": "16 + 4 deg(v) (1+weighted) + 4 per real transition",

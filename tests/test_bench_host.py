@@ -81,3 +81,13 @@ def test_ingest_takes_every_instance_of_the_kernel(tmp_path):
     d = json.load(open(bench.ingest_ncu(str(tmp_path / "l.csv"), str(tmp_path / "b.json"), str(tmp_path))))
     assert d["kernel_launches_per_call"] == 2
     assert d["dram_bytes_per_launch"] == 50 + 51 + 2 * 2
+
+
+def test_dram_fraction():
+    """The R-MAT 26 capture: 144.91 TB a call over 35.873 s is 59% of 6,798.9 GB/s."""
+    d = bench.dram_fraction(144_910_358_544_640, [35_872.9], 6798.9)
+    assert abs(d["achieved"] - 4039.6) < 1.0 and abs(d["frac"] - 0.594) < 0.001
+    assert bench.dram_fraction(None, [1.0], 6798.9) is None
+    assert bench.dram_fraction(10, [], 6798.9) is None
+    two = bench.dram_fraction(2e9, [1.0, 3.0], 1000.0)  # per-call bytes, mean over two calls
+    assert abs(two["achieved"] - 1000.0) < 1e-9  # 4 GB in 4 ms
